@@ -1,0 +1,317 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and the mathematics.
+
+Each test names what it pins; together they are chosen so that a dropped
+term, a wrong sign or index, or a transposed operand anywhere in the oracle
+fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_problem(n=12, p=3, k=3, seed=5, missing=0.0):
+    X, _ = synth.gaussian_mixture(n, p, 3, seed=seed)
+    X = X.astype(np.float64)
+    mask = None
+    if missing > 0:
+        rng = np.random.default_rng(seed + 100)
+        mask = synth.random_mask(rng, n, p, missing)
+        mask[:, 0] = 1  # keep every row with data
+    ei, ej, w, _, _ = O.knn_gaussian_weights(X, mask, k, 0.1, False)
+    return X, mask, O.EdgeGraph(n, ei, ej, w)
+
+
+# --------------------------------------------------------------- two points
+@pytest.mark.parametrize("mu,eps_rel", [(0.05, 1e-2), (0.4, 1e-2), (0.05, 1e-3), (2.0, 1e-2), (0.3, 0.3)])
+def test_two_point_closed_form(mu, eps_rel):
+    """Pins projection (1/3 factor), d_m, the U update and the V prox at once."""
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(2, 4))
+    w = 0.7
+    G = O.EdgeGraph(2, [0], [1], [w])
+    Y0 = O.fill_missing(X, None)
+    rho, eps = O.pd_constants(Y0, G.w, mu, 2.0, eps_rel)
+    U, V, d, fused, it, res, ok = O.solve_gamma(X, None, G, mu, rho, eps, X, np.zeros((1, 4)),
+                                               tol=1e-14, max_iter=400000)
+    assert ok
+    Delta = X[0] - X[1]
+    Dn = np.linalg.norm(Delta)
+    delta, v, fz = pins.two_point_fixed_point(Dn, mu, w, rho, eps)
+    e = Delta / Dn
+    xbar = X.mean(axis=0)
+    U_ref = np.vstack([xbar + 0.5 * delta * e, xbar - 0.5 * delta * e])
+    assert bool(fused[0]) == fz
+    assert np.allclose(U, U_ref, rtol=0, atol=1e-9 * Dn)
+    assert np.allclose(V[0], v * e, rtol=0, atol=1e-9 * Dn)
+
+
+def test_two_point_tends_to_eq1_solution():
+    """As eps -> 0 the PD fixed point tends to the two-point solution of Eq. 1."""
+    D, w, rho = 3.0, 1.0, 20.0
+    for mu in (0.3, 1.0, 2.0):
+        exact = D * max(0.0, 1.0 - 2.0 * mu * w / D)
+        errs = [abs(pins.two_point_fixed_point(D, mu, w, rho, eps)[0] - exact) for eps in (1e-2, 1e-4, 1e-8)]
+        assert errs[2] < 1e-3 and (errs[2] < errs[0] or errs[0] < 1e-12)
+
+
+# --------------------------------------------------------------- projection
+def test_projection_matches_paper_block_descent():
+    """The exact projection equals the paper's Gauss-Seidel block updates run to rest."""
+    X, _, G = small_problem(n=9, p=2, k=2, seed=3)
+    rng = np.random.default_rng(2)
+    U = rng.normal(size=X.shape)
+    V = rng.normal(size=(G.m, X.shape[1]))
+    A, B = O.project(U, V, G)
+    A2, B2 = pins.gauss_seidel_projection(U, V, G.ei, G.ej)
+    assert np.allclose(A, A2, atol=1e-10)
+    assert np.allclose(B, B2, atol=1e-10)
+
+
+def test_projection_stationarity_and_idempotence():
+    X, _, G = small_problem(n=10, p=3, k=3, seed=4)
+    rng = np.random.default_rng(3)
+    U = rng.normal(size=X.shape)
+    V = rng.normal(size=(G.m, 3))
+    A, B = O.project(U, V, G)
+    # the paper's stationarity equations, node by node
+    for i in range(G.n):
+        r = A[i] - U[i]
+        for e in range(G.m):
+            a, b = G.ei[e], G.ej[e]
+            if a == i:
+                r += A[i] - A[b] - V[e]
+            elif b == i:
+                r -= A[a] - A[i] - V[e]
+        assert np.max(np.abs(r)) < 1e-10
+    A2, B2 = O.project(A, B, G)
+    assert np.allclose(A2, A, atol=1e-12) and np.allclose(B2, B, atol=1e-12)
+    # and the dense orthogonal projector agrees
+    P = pins.projection_matrix(G.n, G.ei, G.ej)
+    Z = P @ np.vstack([U, V])
+    assert np.allclose(Z[:G.n], A, atol=1e-10) and np.allclose(Z[G.n:], B, atol=1e-10)
+
+
+def test_projection_complete_graph_closed_form():
+    """Complete graph: (I + L) = (1+n) I - 11^T, so A = (R + 1 1^T R) / (1 + n)."""
+    n, p = 7, 3
+    ei, ej = np.triu_indices(n, 1)
+    G = O.EdgeGraph(n, ei, ej, np.ones(ei.size))
+    rng = np.random.default_rng(4)
+    U = rng.normal(size=(n, p))
+    V = rng.normal(size=(G.m, p))
+    R = U + pins.incidence(n, ei, ej).T @ V
+    A_ref = (R + R.sum(axis=0, keepdims=True)) / (1 + n)
+    A, _ = O.project(U, V, G)
+    assert np.allclose(A, A_ref, atol=1e-12)
+
+
+# --------------------------------------------------------------- MM step
+@pytest.mark.parametrize("missing", [0.0, 0.2])
+def test_literal_mm_monotone(missing):
+    """Each literal MM step does not increase the approximate objective (MM principle)."""
+    X, mask, G = small_problem(n=12, p=3, k=3, seed=6, missing=missing)
+    Y0 = O.fill_missing(X, mask)
+    mu = 0.5
+    rho, eps = O.pd_constants(Y0, G.w, mu)
+    U, V = Y0.copy(), np.zeros((G.m, 3))
+    f = O.objective(U, V, X, mask, G, mu, rho, eps)
+    for _ in range(300):
+        U, V, _, _ = O.mm_step(U, V, X, mask, G, mu, rho, eps)
+        f2 = O.objective(U, V, X, mask, G, mu, rho, eps)
+        assert f2 <= f + 1e-12 * abs(f)
+        f = f2
+
+
+def test_prox_is_optimal():
+    """The V update minimises mu w ||v|| + rho/(2 d) ||v - b||^2; b = 0 gives v = 0."""
+    from scipy.optimize import minimize
+    X, _, G = small_problem(n=8, p=3, k=2, seed=7)
+    rng = np.random.default_rng(5)
+    U = X + 0.3 * rng.normal(size=X.shape)
+    V = rng.normal(size=(G.m, 3))
+    mu, rho, eps = 0.8, 5.0, 1e-2
+    _, Vn, d, fused = O.mm_step(U, V, X, None, G, mu, rho, eps)
+    _, B = O.project(U, V, G)
+    for e in range(G.m):
+        def obj(v):
+            return mu * G.w[e] * np.linalg.norm(v) + rho / (2 * d) * np.sum((v - B[e]) ** 2)
+        best = minimize(obj, B[e], method="Nelder-Mead", options={"xatol": 1e-12, "fatol": 1e-15, "maxiter": 20000}).x
+        assert obj(Vn[e]) <= obj(best) + 1e-10
+    # zero difference gives zero
+    G2 = O.EdgeGraph(2, [0], [1], [1.0])
+    Xs = np.ones((2, 2))
+    _, V2, _, f2 = O.mm_step(Xs, np.zeros((1, 2)), Xs, None, G2, 1.0, 3.0, 1e-4)
+    assert f2[0] and np.all(V2 == 0)
+
+
+def test_fixed_point_satisfies_kkt_of_smoothed_objective():
+    """The oracle's result minimises F (plain definition of the PD fixed point)."""
+    for missing in (0.0, 0.15):
+        X, mask, G = small_problem(n=10, p=2, k=3, seed=8, missing=missing)
+        Y0 = O.fill_missing(X, mask)
+        for mu in (0.2, 3.0):
+            rho, eps = O.pd_constants(Y0, G.w, mu, 2.0, 1e-2)
+            U, V, d, fused, it, res, ok = O.solve_gamma(X, mask, G, mu, rho, eps, Y0, np.zeros((G.m, 2)),
+                                                       tol=1e-13, max_iter=400000)
+            assert ok
+            r = pins.kkt_residual(U, V, X, mask, G.ei, G.ej, G.w, mu, rho, eps, fused)
+            assert r < 1e-7, (missing, mu, r)
+
+
+def test_literal_and_accelerated_reach_same_fixed_point():
+    X, _, G = small_problem(n=8, p=2, k=2, seed=9)
+    mu = 0.5
+    rho, eps = O.pd_constants(X, G.w, mu, 2.0, 0.2)
+    a = O.solve_gamma(X, None, G, mu, rho, eps, X, np.zeros((G.m, 2)), tol=1e-12, accelerate=True)
+    b = O.solve_gamma(X, None, G, mu, rho, eps, X, np.zeros((G.m, 2)), tol=1e-12, accelerate=False,
+                      max_iter=2_000_000)
+    assert a[6] and b[6]
+    assert np.allclose(a[0], b[0], atol=1e-8)
+
+
+# --------------------------------------------------------------- special cases / invariances
+def test_mu_zero_gives_data():
+    X, _, G = small_problem(n=10, p=3, k=3, seed=10)
+    path = O.solve_path(X, None, G, [0.0], tol=1e-12)
+    assert np.allclose(path[0].U, X, atol=1e-9)
+    assert not path[0].fused.any()
+
+
+def test_large_mu_fuses_connected_graph_to_mean():
+    X, _, G = small_problem(n=10, p=3, k=4, seed=11)
+    labels_graph = O.fused_labels(G.n, G.ei, G.ej, np.ones(G.m, bool))
+    assert labels_graph.max() == 0  # connected
+    path = O.solve_path(X, None, G, [1e4], tol=1e-12)
+    r = path[0]
+    assert r.fused.all() and (r.labels == 0).all()
+    Xc = X - X.mean(axis=0)
+    # full fusion up to the eps smoothing bias (order eps_rel)
+    assert np.linalg.norm(r.U - X.mean(axis=0)) <= 1e-2 * np.linalg.norm(Xc)
+
+
+def test_mean_preserved_every_iterate_and_at_fixed_point():
+    """Sum of u_i equals sum of x_i (no missing data): the exact projection keeps
+    1^T A = 1^T U, and the U update is a convex combination with X."""
+    X, _, G = small_problem(n=11, p=3, k=3, seed=12)
+    mu = 1.0
+    rho, eps = O.pd_constants(X, G.w, mu)
+    U, V = X.copy(), np.zeros((G.m, 3))
+    for _ in range(50):
+        U, V, _, _ = O.mm_step(U, V, X, None, G, mu, rho, eps)
+        assert np.allclose(U.mean(axis=0), X.mean(axis=0), atol=1e-12)
+
+
+def test_weight_rescaling_equals_mu_rescaling():
+    """U(mu, c w) = U(c mu, w) (normalising weights is equivalent to rescaling mu)."""
+    X, _, G = small_problem(n=10, p=2, k=3, seed=13)
+    c = 3.7
+    G2 = O.EdgeGraph(G.n, G.ei, G.ej, c * G.w)
+    a = O.solve_path(X, None, G2, [0.4], tol=1e-13)[0]
+    b = O.solve_path(X, None, G, [0.4 * c], tol=1e-13)[0]
+    assert np.allclose(a.U, b.U, atol=1e-9)
+    assert (a.fused == b.fused).all()
+
+
+def test_equivariance_translation_rotation_permutation():
+    X, _, G = small_problem(n=9, p=3, k=3, seed=14)
+    mu = 0.8
+    base = O.solve_path(X, None, G, [mu], tol=1e-13)[0]
+    t = np.array([5.0, -2.0, 1.5])
+    tr = O.solve_path(X + t, None, G, [mu], tol=1e-13)[0]
+    assert np.allclose(tr.U, base.U + t, atol=1e-8)
+    Q, _ = np.linalg.qr(np.random.default_rng(0).normal(size=(3, 3)))
+    ro = O.solve_path(X @ Q, None, G, [mu], tol=1e-13)[0]
+    assert np.allclose(ro.U, base.U @ Q, atol=1e-8)
+    perm = np.random.default_rng(1).permutation(G.n)
+    inv = np.argsort(perm)            # new index of old case i is inv[i]
+    a, b = inv[G.ei], inv[G.ej]
+    G3 = O.EdgeGraph(G.n, np.minimum(a, b), np.maximum(a, b), G.w)
+    pe = O.solve_path(X[perm], None, G3, [mu], tol=1e-13)[0]
+    assert np.allclose(pe.U, base.U[perm], atol=1e-8)
+
+
+def test_all_observed_mask_is_unmasked_solver():
+    X, _, G = small_problem(n=9, p=3, k=3, seed=15)
+    a = O.solve_path(X, None, G, [0.3, 1.2], tol=1e-12)
+    b = O.solve_path(X, np.ones(X.shape, np.uint8), G, [0.3, 1.2], tol=1e-12)
+    for r1, r2 in zip(a, b):
+        assert np.array_equal(r1.U, r2.U) and np.array_equal(r1.fused, r2.fused)
+
+
+def test_disconnected_components_never_merge():
+    X1, _ = synth.gaussian_mixture(6, 2, 1, seed=1)
+    X = np.vstack([X1, X1 + 100.0]).astype(np.float64)
+    ei = [0, 1, 2, 3, 4, 6, 7, 8, 9, 10]
+    ej = [1, 2, 3, 4, 5, 7, 8, 9, 10, 11]
+    G = O.EdgeGraph(12, ei, ej, np.ones(10))
+    r = O.solve_path(X, None, G, [1e3], tol=1e-12)[0]
+    assert set(r.labels[:6]) == {0} and set(r.labels[6:]) == {1}
+
+
+# --------------------------------------------------------------- true minimiser of Eq. 1
+def test_pd_fixed_point_approaches_convex_clustering_minimizer():
+    """As eps -> 0 the PD fixed point tends to the unique minimiser of Eq. 1."""
+    X, _, G = small_problem(n=8, p=2, k=3, seed=16)
+    mu = 0.6
+    Ustar, gap = pins.convex_clustering_minimizer(X, G.ei, G.ej, G.w, mu)
+    assert gap < 1e-9
+    errs = []
+    for eps_rel in (1e-1, 1e-2, 1e-3):
+        r = O.solve_path(X, None, G, [mu], eps_rel=eps_rel, tol=1e-13)[0]
+        errs.append(np.linalg.norm(r.U - Ustar) / np.linalg.norm(Ustar))
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 2e-3
+
+
+# --------------------------------------------------------------- weights and labels
+def _golden_knn():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "knn_line.txt")) if ln.strip() and not ln.startswith("#")]
+    out = {}
+    for c, i, j, d2, w in rows:
+        out.setdefault(c, []).append((int(i), int(j), float(d2), float(w)))
+    return out
+
+
+def test_knn_weights_hand_example():
+    g = _golden_knn()
+    X = np.array([[0.0], [1.0], [3.0], [7.0]])
+    ei, ej, w, d2, _ = O.knn_gaussian_weights(X, None, 1, 0.5, False)
+    assert [(a, b) for a, b, _, _ in g["A"]] == list(zip(ei.tolist(), ej.tolist()))
+    assert np.allclose(d2, [r[2] for r in g["A"]], rtol=0, atol=0)
+    assert np.allclose(w, [r[3] for r in g["A"]], rtol=1e-15)
+    X = np.array([[0.0], [1.0], [2.0]])
+    ei, ej, w, d2, _ = O.knn_gaussian_weights(X, None, 1, 0.0, True)
+    assert [(a, b) for a, b, _, _ in g["B"]] == list(zip(ei.tolist(), ej.tolist()))
+    assert np.allclose(w, [r[3] for r in g["B"]], rtol=1e-15)
+
+
+def test_knn_union_properties():
+    X, _ = synth.gaussian_mixture(40, 5, 3, seed=2)
+    ei, ej, w, d2, _ = O.knn_gaussian_weights(X, None, 4, 0.3, True)
+    n = 40
+    deg = np.bincount(ei, minlength=n) + np.bincount(ej, minlength=n)
+    assert deg.min() >= 4 and np.all(ei < ej)
+    assert abs(w.sum() - 1.0) < 1e-12
+    # exact distances
+    Xd = X.astype(np.float64)
+    assert np.allclose(d2, np.sum((Xd[ei] - Xd[ej]) ** 2, axis=1), rtol=1e-14)
+    # every listed neighbour of i is at least as close as every non-neighbour
+    D2 = np.sum((Xd[:, None] - Xd[None]) ** 2, axis=-1)
+    for i in range(n):
+        nb = set(ej[ei == i].tolist()) | set(ei[ej == i].tolist())
+        kth = np.sort(np.delete(D2[i], i))[3]
+        near = [j for j in range(n) if j != i and D2[i, j] < kth]
+        assert set(near) <= nb
+
+
+def test_fused_labels_canonical():
+    lab = O.fused_labels(6, [0, 1, 2, 3], [1, 2, 4, 5], [False, True, False, True])
+    # components: {0}, {1,2}, {3,5}, {4}
+    assert lab.tolist() == [0, 1, 1, 2, 3, 2]
