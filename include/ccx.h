@@ -1,0 +1,204 @@
+/*
+ * ccx.h -- C ABI of a GB300 (sm_103a) solver for convex clustering by the
+ * proximal distance (PD) algorithm of Chen, Chi, Ranola and Lange,
+ * "Convex Clustering: An Attractive Alternative to Hierarchical Clustering"
+ * (arXiv:1409.2065).
+ *
+ * Problem (Methods, Eq. 1 and, with missing entries, Eq. 6):
+ *   minimise_U  1/2 sum_{(i,c) observed} (x_ic - u_ic)^2 + mu sum_{i<j} w_ij ||u_i - u_j||
+ * over centroids u_i, one per case (row) x_i of the n x p data matrix X.
+ * The library computes, for each penalty mu of a user grid (the paper's
+ * mu; this header calls it gamma), the fixed point of the paper's PD/MM map
+ * (Methods, "The Proximal Distance Algorithm": the projection onto
+ * C = {v_ij = u_i - u_j}, the smoothed distance d_m of Eq. 5, the U update
+ * and the block soft-threshold V update; "Missing Data": Y = X on observed
+ * entries and the current U elsewhere), warm-starting each gamma from the
+ * previous one.  Fused edges are those whose V update returns exactly zero
+ * (gamma w_ij d >= rho ||b_ij||); clusters are the connected components of
+ * the fused edges, labelled 0.. by the rank of their smallest member.
+ *
+ * Conventions for every call:
+ *  - Every function returns a ccx_status.  On failure nothing the caller
+ *    owns is freed; ccx_last_error() returns a thread-local message.
+ *  - Arrays are row-major.  "host or device" pointers are classified with
+ *    cudaPointerGetAttributes; device pointers must be on the device that
+ *    was current when the problem was created.
+ *  - The caller owns every array it passes.  The library copies inputs at
+ *    the call and never keeps a caller pointer after returning.
+ *  - All GPU work of a problem runs on the stream given at creation (NULL =
+ *    the legacy default stream); calls that return results synchronise that
+ *    stream before returning.
+ *  - A ccx_problem may be used by one host thread at a time.
+ */
+#ifndef CCX_H
+#define CCX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ccx_problem ccx_problem;
+
+typedef enum {
+    CCX_OK = 0,
+    CCX_EINVAL = 1,       /* invalid argument; message says which */
+    CCX_ENOMEM = 2,       /* device or host allocation failed */
+    CCX_ECUDA = 3,        /* a CUDA runtime call failed */
+    CCX_ENOTCONV = 4,     /* max_iter reached for some gamma; outputs are still written */
+    CCX_ETIMEOUT = 5,     /* a bounded wait ran out (server); nothing was lost */
+    CCX_ECANCELLED = 6,   /* job cancelled before it ran */
+    CCX_EUNSUPPORTED = 7  /* size outside what this build handles; message gives the limit */
+} ccx_status;
+
+enum { CCX_FP32 = 0, CCX_FP64 = 1 };
+
+/*
+ * k-nearest-neighbour Gaussian-kernel weights (Calibration of Weights,
+ * Eq. 8): w_ij = 1{i ~_k j} exp(-phi ||x_i - x_j||^2), where i ~_k j when j
+ * is among the k nearest other cases of i or i among those of j (ties go to
+ * the smaller index).  Missing entries are filled with their column's
+ * observed mean for this purpose only.  phi_auto != 0 takes
+ * phi = 1 / median ||x_i - x_j||^2 over the union edges.  normalize != 0
+ * scales the weights to sum to 1 over i < j (the paper normalises them;
+ * this is equivalent to rescaling gamma).  Edges of weight exactly 0 are dropped.
+ */
+typedef struct {
+    int k;          /* neighbours per case, 1 <= k; k >= n-1 gives all pairs */
+    double phi;     /* >= 0, used when phi_auto == 0 */
+    int phi_auto;
+    int normalize;
+} ccx_knn_rule;
+
+/*
+ * Solver options.  The paper fixes neither rho (only that it must exceed a
+ * Lipschitz constant of the loss) nor eps (only that it is a small positive
+ * number); the library takes rho = rho_scale (||Y_c||_F + gamma ||w||_2) and
+ * eps = (eps_rel ||Y_c||_F)^2 with Y_c the column-centred start matrix.
+ */
+typedef struct {
+    double rho_scale;  /* default 2 */
+    double eps_rel;    /* default 1e-3 */
+    double tol;        /* stop when the estimated error of U is <= tol ||U||_F; default 1e-6 (FP32), 1e-10 (FP64) */
+    int max_iter;      /* MM iterations per gamma; default 200000 */
+    int accelerate;    /* 1: Nesterov-extrapolated MM with restarts (default); 0: the plain MM iteration */
+    int chunk;         /* iterations per captured CUDA graph launch; default 64 */
+} ccx_opts;
+
+/* Per-gamma statistics. */
+typedef struct {
+    int iters;         /* MM iterations spent on this gamma */
+    int converged;     /* 1: error estimate <= tol; 2: stopped because the iterate only moves at the
+                          rounding level (no 10 % progress for a long stretch); 0: max_iter reached */
+    int n_fused;       /* fused edges at the returned iterate */
+    int n_clusters;    /* connected components of the fused edges */
+    double gamma, rho, eps;
+    double d_final;    /* d_m of the last iteration */
+    double err_est;    /* estimated relative error of U at stop */
+    double seconds;    /* wall time of this gamma, including its output copies */
+} ccx_gamma_stats;
+
+/* Fill *o with the defaults listed above. */
+void ccx_opts_default(ccx_opts* o);
+
+/*
+ * Create a problem from the n x p data matrix X (Methods: n cases, p
+ * predictors; rows are cases).
+ *   X     : n rows of p floats, row stride ld >= p floats; host or device.
+ *   mask  : NULL (all observed) or n rows of p bytes, stride ld; 1 = observed,
+ *           0 = missing (Missing Data, the set Gamma).  Host or device.
+ *   n, p  : n >= 1, p >= 1.
+ *   stream: cudaStream_t for all work of this problem, or NULL.
+ *   precision: CCX_FP32 or CCX_FP64 (FP64 keeps a double copy of X).
+ * Errors: CCX_EINVAL for bad sizes, a non-finite observed entry, or a row
+ * with no observed entry; CCX_ENOMEM; CCX_ECUDA.
+ */
+ccx_status ccx_problem_create(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld,
+                              int precision, void* stream, ccx_problem** out);
+
+/*
+ * Set the weighted edge set explicitly (host arrays): edge e joins cases
+ * ei[e] < ej[e] with weight w[e] >= 0 (Methods: the set E of pairs with
+ * positive weight).  Zero-weight edges are dropped.  Replaces any earlier
+ * edge set.  CCX_EINVAL on an index out of range, ei >= ej, a duplicate
+ * pair, or a negative or non-finite weight.
+ */
+ccx_status ccx_set_edges(ccx_problem* pr, int64_t n_edges, const int32_t* ei, const int32_t* ej,
+                         const double* w);
+
+/*
+ * Build the edge set on the GPU by the kNN Gaussian-kernel rule above
+ * (Eq. 8).  Candidate neighbours come from a Gram matrix on the tensor
+ * cores; their distances are recomputed exactly (double) before the k
+ * nearest are chosen.  Replaces any earlier edge set.
+ */
+ccx_status ccx_build_knn(ccx_problem* pr, const ccx_knn_rule* rule);
+
+/*
+ * Copy the current edge set out (host arrays, sorted by (ei, ej)).  With
+ * ei == NULL only *n_edges is written (size query).  Otherwise *n_edges must
+ * hold the capacity on entry and receives the count.
+ */
+ccx_status ccx_get_edges(const ccx_problem* pr, int64_t* n_edges, int32_t* ei, int32_t* ej, double* w);
+
+/*
+ * Median over edges of ||y_i - y_j|| / (2 w_ij) (Y = X with missing entries
+ * at column means): the gamma at which an isolated pair would fuse under
+ * Eq. 1.  Used to place a gamma grid.  CCX_EINVAL without edges.
+ */
+ccx_status ccx_fusion_scale(const ccx_problem* pr, double* gamma0);
+
+/*
+ * Solve the warm-started path over gammas[0..n_gamma-1] in the order given
+ * (Evaluation of Clusters: the program minimises over a user-given grid of mu).
+ *   gammas    : host array, each finite and >= 0.
+ *   opts      : NULL for defaults.
+ *   U_out     : NULL, or n_gamma x n x ld floats (ld of the creation call),
+ *               host or device; gamma g writes rows [g*n, (g+1)*n).
+ *   labels_out: NULL, or n_gamma x n int32, host or device.
+ *   stats     : NULL, or n_gamma host structs.
+ * The first gamma starts from U = Y_0 (missing entries at their column's
+ * observed mean) and V = 0; with a second call the path continues from
+ * where the previous call stopped.  Returns CCX_ENOTCONV (outputs written)
+ * when some gamma hit max_iter.  CCX_EUNSUPPORTED beyond this build's
+ * on-chip limits (the message gives them).
+ */
+ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts,
+                          float* U_out, int32_t* labels_out, ccx_gamma_stats* stats);
+
+/* Forget the warm-start state: the next ccx_solve_path starts from Y_0, V = 0. */
+ccx_status ccx_reset_path(ccx_problem* pr);
+
+/* Release all device and host memory of the problem (NULL is accepted). */
+ccx_status ccx_problem_destroy(ccx_problem* pr);
+
+/*
+ * Instrumentation (no counterpart in the paper).  Runs n_iter MM iterations of
+ * the problem's current warm-start state at penalty gamma with the stopping
+ * test disabled, launching each iteration's two kernels individually and
+ * timing them with CUDA events on the stream they run on.  Returns the mean
+ * duration in milliseconds of the fused node/edge kernel (slice_ms) and of
+ * the reduction kernel (reduce_ms).  The path state advances: a following
+ * ccx_solve_path continues from it.  opts as in ccx_solve_path (NULL =
+ * defaults).
+ */
+ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts, double* slice_ms,
+                               double* reduce_ms);
+
+/* Number of GPU kernels this library has launched in the process so far
+ * (all problems; kernels inside CUDA-graph launches are counted). */
+uint64_t ccx_kernel_launches(void);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* ccx_last_error(void);
+
+/* Library version string. */
+const char* ccx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCX_H */

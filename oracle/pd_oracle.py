@@ -72,7 +72,7 @@ class EdgeGraph:
     """Undirected weighted edge set {i, j}, i < j, w_ij > 0.
 
     Zero weights are dropped: the paper introduces no difference vector for
-    them ("computationally foolish").  Holds the incidence matrix D (one row
+    them, since they would add work without changing the objective.  Holds the incidence matrix D (one row
     per edge, +1 at i, -1 at j), so that (D U)_e = u_i - u_j and
     (D^T V)_i = sum_{j in R_i} v_ij - sum_{j in L_i} v_ji.
     """
@@ -326,8 +326,10 @@ def knn_gaussian_weights(X, mask, k: int, phi, normalize: bool):
     """
     Y = fill_missing(X, mask)
     n = Y.shape[0]
-    diff = Y[:, None, :] - Y[None, :, :]
-    D2 = np.einsum("ijk,ijk->ij", diff, diff)
+    D2 = np.empty((n, n))
+    for i in range(n):                      # one row at a time keeps memory at n x p
+        diff = Y - Y[i]
+        D2[i] = np.einsum("jk,jk->j", diff, diff)
     kk = min(k, n - 1)
     pairs = set()
     for i in range(n):

@@ -1,0 +1,246 @@
+"""Thin Python binding of the ccx C ABI (include/ccx.h).
+
+Argument marshalling only: every step of the solver runs in libccx.so.  The
+functions keep the C names without the ``ccx_`` prefix.  Arrays may be numpy
+arrays (host) or torch tensors (host or CUDA); outputs are allocated as numpy
+arrays, or as CUDA torch tensors when ``device=True``.
+
+Importing this module loads the compiled library and raises ImportError if
+it has not been built (``__graft_entry__.build()`` or
+``python paper_1409_2065_gb300/build.py``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libccx.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"ccx CUDA library not built ({LIB_PATH} missing); run __graft_entry__.build()")
+_lib = C.CDLL(LIB_PATH)
+
+CCX_FP32, CCX_FP64 = 0, 1
+STATUS = {0: "CCX_OK", 1: "CCX_EINVAL", 2: "CCX_ENOMEM", 3: "CCX_ECUDA", 4: "CCX_ENOTCONV",
+          5: "CCX_ETIMEOUT", 6: "CCX_ECANCELLED", 7: "CCX_EUNSUPPORTED"}
+
+
+class KnnRule(C.Structure):
+    _fields_ = [("k", C.c_int), ("phi", C.c_double), ("phi_auto", C.c_int), ("normalize", C.c_int)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("rho_scale", C.c_double), ("eps_rel", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("accelerate", C.c_int), ("chunk", C.c_int)]
+
+
+class GammaStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("n_fused", C.c_int), ("n_clusters", C.c_int),
+                ("gamma", C.c_double), ("rho", C.c_double), ("eps", C.c_double), ("d_final", C.c_double),
+                ("err_est", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_sigs = {
+    "ccx_opts_default": (None, [C.POINTER(Opts)]),
+    "ccx_problem_create": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int, _P, C.POINTER(_P)]),
+    "ccx_set_edges": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
+    "ccx_build_knn": (C.c_int, [_P, C.POINTER(KnnRule)]),
+    "ccx_get_edges": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P]),
+    "ccx_fusion_scale": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
+    "ccx_reset_path": (C.c_int, [_P]),
+    "ccx_problem_destroy": (C.c_int, [_P]),
+    "ccx_time_iterations": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]),
+    "ccx_kernel_launches": (C.c_uint64, []),
+    "ccx_last_error": (C.c_char_p, []),
+    "ccx_version": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+# every symbol the header declares, for the export check in the tests
+EXPORTED = tuple(_sigs)
+
+
+class CcxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def last_error() -> str:
+    return _lib.ccx_last_error().decode()
+
+
+def version() -> str:
+    return _lib.ccx_version().decode()
+
+
+def _check(st: int, allow=(0,)) -> int:
+    if st not in allow:
+        raise CcxError(st, last_error())
+    return st
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) for a numpy array or torch tensor of the given numpy dtype."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        tdt = {np.float32: torch.float32, np.uint8: torch.uint8, np.int32: torch.int32,
+               np.float64: torch.float64}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            x = x.to(tdt).contiguous()
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+def opts_default() -> Opts:
+    o = Opts()
+    _lib.ccx_opts_default(C.byref(o))
+    return o
+
+
+def problem_create(X, mask=None, precision=CCX_FP32, stream=None):
+    """Create a problem from X (n x p).  Returns an opaque handle (int)."""
+    n, p = int(X.shape[0]), int(X.shape[1])
+    xp, xk = _ptr(X, np.float32)
+    mp, mk = _ptr(mask, np.uint8)
+    h = _P()
+    st = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+    _check(_lib.ccx_problem_create(xp, mp, n, p, p, int(precision), st, C.byref(h)))
+    del xk, mk
+    return h.value
+
+
+def problem_destroy(h) -> None:
+    _check(_lib.ccx_problem_destroy(h))
+
+
+def set_edges(h, ei, ej, w) -> None:
+    ei = np.ascontiguousarray(ei, dtype=np.int32)
+    ej = np.ascontiguousarray(ej, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    _check(_lib.ccx_set_edges(h, ei.size, ei.ctypes.data, ej.ctypes.data, w.ctypes.data))
+
+
+def build_knn(h, k: int, phi: float = 0.0, phi_auto: bool = False, normalize: bool = False) -> None:
+    r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)))
+    _check(_lib.ccx_build_knn(h, C.byref(r)))
+
+
+def get_edges(h):
+    m = C.c_int64(0)
+    _check(_lib.ccx_get_edges(h, C.byref(m), None, None, None))
+    ei = np.zeros(m.value, np.int32)
+    ej = np.zeros(m.value, np.int32)
+    w = np.zeros(m.value, np.float64)
+    _check(_lib.ccx_get_edges(h, C.byref(m), ei.ctypes.data, ej.ctypes.data, w.ctypes.data))
+    return ei, ej, w
+
+
+def fusion_scale(h) -> float:
+    g = C.c_double(0.0)
+    _check(_lib.ccx_fusion_scale(h, C.byref(g)))
+    return g.value
+
+
+def solve_path(h, gammas, n: int, p: int, opts: Opts | None = None, want_U: bool = True,
+               want_labels: bool = True, device: bool = False, U_out=None, labels_out=None):
+    """Solve the warm-started path.  Returns (U (G x n x p float32), labels (G x n int32), stats list, status).
+
+    With device=True the outputs are CUDA torch tensors written directly by the
+    library; otherwise numpy arrays.  Preallocated outputs may be passed.
+    """
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    G = g.size
+    if device:
+        import torch
+        if want_U and U_out is None:
+            U_out = torch.empty((G, n, p), dtype=torch.float32, device="cuda")
+        if want_labels and labels_out is None:
+            labels_out = torch.empty((G, n), dtype=torch.int32, device="cuda")
+    else:
+        if want_U and U_out is None:
+            U_out = np.empty((G, n, p), np.float32)
+        if want_labels and labels_out is None:
+            labels_out = np.empty((G, n), np.int32)
+    up, _ = _ptr(U_out, np.float32) if U_out is not None else (None, None)
+    lp, _ = _ptr(labels_out, np.int32) if labels_out is not None else (None, None)
+    stats = (GammaStats * max(G, 1))()
+    o = C.byref(opts) if opts is not None else None
+    st = _check(_lib.ccx_solve_path(h, g.ctypes.data, G, o, up, lp, stats), allow=(0, 4))
+    return U_out, labels_out, [stats[k].as_dict() for k in range(G)], st
+
+
+def reset_path(h) -> None:
+    _check(_lib.ccx_reset_path(h))
+
+
+def time_iterations(h, gamma: float, n_iter: int, opts: Opts | None = None):
+    """(mean ms of the fused iteration kernel, mean ms of the reduction kernel) over n_iter iterations."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    o = C.byref(opts) if opts is not None else None
+    _check(_lib.ccx_time_iterations(h, float(gamma), int(n_iter), o, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def kernel_launches() -> int:
+    return int(_lib.ccx_kernel_launches())
+
+
+class Problem:
+    """Owning wrapper around a problem handle."""
+
+    def __init__(self, X, mask=None, precision=CCX_FP32, stream=None):
+        self.n, self.p = int(X.shape[0]), int(X.shape[1])
+        self.h = problem_create(X, mask, precision, stream)
+
+    def set_edges(self, ei, ej, w):
+        set_edges(self.h, ei, ej, w)
+
+    def build_knn(self, k, phi=0.0, phi_auto=False, normalize=False):
+        build_knn(self.h, k, phi, phi_auto, normalize)
+
+    def get_edges(self):
+        return get_edges(self.h)
+
+    def fusion_scale(self):
+        return fusion_scale(self.h)
+
+    def solve_path(self, gammas, opts=None, **kw):
+        return solve_path(self.h, gammas, self.n, self.p, opts, **kw)
+
+    def reset_path(self):
+        reset_path(self.h)
+
+    def time_iterations(self, gamma, n_iter, opts=None):
+        return time_iterations(self.h, gamma, n_iter, opts)
+
+    def close(self):
+        if self.h:
+            problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

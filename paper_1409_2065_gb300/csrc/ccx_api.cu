@@ -1,0 +1,787 @@
+// C ABI of the convex-clustering solver (include/ccx.h) and its host runtime:
+// input validation, device buffers, the warm-started gamma path driven by a
+// captured CUDA graph of MM iterations, per-gamma outputs and labels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ccx_internal.h"
+
+namespace ccx {
+void knn_set_exact_rows(const float* Xf, const uint32_t* bits, const double* colmean, int ldw);
+int reduce_blocks(int m);
+}  // namespace ccx
+
+using namespace ccx;
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void ccx::count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_err;
+
+ccx_status fail(ccx_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess) {                                                                \
+            if (_e == cudaErrorMemoryAllocation)                                                \
+                return fail(CCX_ENOMEM, "%s: %s", #expr, cudaGetErrorString(_e));               \
+            return fail(CCX_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(_e));             \
+        }                                                                                       \
+    } while (0)
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+}
+
+}  // namespace
+
+struct ccx_problem {
+    int device = 0;
+    cudaStream_t user = nullptr;
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_user = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
+    int precision = CCX_FP32;
+    int64_t n = 0, p = 0, ld_in = 0;
+    int ld = 0, ldw = 0, nslices = 0, G = 0, num_sms = 0;
+    bool has_mask = false;
+    // data
+    float* Xf = nullptr;
+    double* Xd = nullptr;
+    uint32_t* maskbits = nullptr;
+    double* colmean = nullptr;   // 2 * ld doubles (means, then per-column scratch)
+    float* Y0f = nullptr;
+    double* Y0d = nullptr;
+    double* d_ss = nullptr;
+    double nyc = 0.0;            // ||Y_c||_F
+    double ny0 = 0.0;            // ||Y_0||_F
+    // edges
+    std::vector<int> ei, ej;
+    std::vector<double> w;
+    double nw = 0.0;             // ||w||_2
+    int deg_max = 0;
+    int* d_ei = nullptr;
+    int* d_ej = nullptr;
+    double* d_w = nullptr;
+    int* d_rowptr = nullptr;
+    int* d_col = nullptr;
+    int* d_eid = nullptr;
+    // path state
+    void* A[2] = {nullptr, nullptr};
+    float* Alo[2] = {nullptr, nullptr};
+    void* Dl[2] = {nullptr, nullptr};
+    void* Q = nullptr;
+    void* Em = nullptr;
+    void* t[2] = {nullptr, nullptr};
+    double* Pnb = nullptr;
+    double* Ps = nullptr;
+    double* nb = nullptr;
+    uint8_t* fused = nullptr;
+    unsigned long long* Rf = nullptr;
+    PdState* st = nullptr;
+    PdState* st_host = nullptr;  // pinned, 2 slots
+    float* Ustage = nullptr;
+    int* Lstage = nullptr;
+    int* cc_scratch = nullptr;
+    int* d_ncl = nullptr;
+    int* h_ncl = nullptr;        // pinned
+    bool path_ready = false;
+    bool path_started = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+};
+
+namespace {
+
+void free_path(ccx_problem* pr) {
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(pr->A[k]);
+        cudaFree(pr->Alo[k]);
+        cudaFree(pr->Dl[k]);
+        cudaFree(pr->t[k]);
+        pr->A[k] = pr->Alo[k] = nullptr;
+        pr->Dl[k] = pr->t[k] = nullptr;
+    }
+    cudaFree(pr->Q);
+    cudaFree(pr->Em);
+    cudaFree(pr->Pnb);
+    cudaFree(pr->Ps);
+    cudaFree(pr->nb);
+    cudaFree(pr->fused);
+    cudaFree(pr->Rf);
+    cudaFree(pr->st);
+    cudaFree(pr->Ustage);
+    cudaFree(pr->Lstage);
+    cudaFree(pr->cc_scratch);
+    cudaFree(pr->d_ncl);
+    if (pr->st_host) cudaFreeHost(pr->st_host);
+    if (pr->h_ncl) cudaFreeHost(pr->h_ncl);
+    if (pr->graph) cudaGraphExecDestroy(pr->graph);
+    pr->Q = pr->Em = nullptr;
+    pr->Pnb = pr->Ps = pr->nb = nullptr;
+    pr->fused = nullptr;
+    pr->Rf = nullptr;
+    pr->st = nullptr;
+    pr->st_host = nullptr;
+    pr->Ustage = nullptr;
+    pr->Lstage = pr->cc_scratch = pr->d_ncl = pr->h_ncl = nullptr;
+    pr->graph = nullptr;
+    pr->graph_chunk = 0;
+    pr->path_ready = false;
+    pr->path_started = false;
+}
+
+void free_edges(ccx_problem* pr) {
+    cudaFree(pr->d_ei);
+    cudaFree(pr->d_ej);
+    cudaFree(pr->d_w);
+    cudaFree(pr->d_rowptr);
+    cudaFree(pr->d_col);
+    cudaFree(pr->d_eid);
+    pr->d_ei = pr->d_ej = pr->d_rowptr = pr->d_col = pr->d_eid = nullptr;
+    pr->d_w = nullptr;
+}
+
+void free_all(ccx_problem* pr) {
+    free_path(pr);
+    free_edges(pr);
+    cudaFree(pr->Xf);
+    cudaFree(pr->Xd);
+    cudaFree(pr->maskbits);
+    cudaFree(pr->colmean);
+    cudaFree(pr->Y0f);
+    cudaFree(pr->Y0d);
+    cudaFree(pr->d_ss);
+    if (pr->ev_user) cudaEventDestroy(pr->ev_user);
+    if (pr->ev_done) cudaEventDestroy(pr->ev_done);
+    for (int k = 0; k < 2; ++k)
+        if (pr->ev_chunk[k]) cudaEventDestroy(pr->ev_chunk[k]);
+    if (pr->work) cudaStreamDestroy(pr->work);
+}
+
+// make the work stream wait for everything already queued on the caller's stream
+ccx_status enter(ccx_problem* pr) {
+    CUDA_TRY(cudaSetDevice(pr->device));
+    CUDA_TRY(cudaEventRecord(pr->ev_user, pr->user));
+    CUDA_TRY(cudaStreamWaitEvent(pr->work, pr->ev_user, 0));
+    return CCX_OK;
+}
+
+// make the caller's stream wait for the work and wait on the host
+ccx_status leave(ccx_problem* pr) {
+    CUDA_TRY(cudaEventRecord(pr->ev_done, pr->work));
+    CUDA_TRY(cudaStreamWaitEvent(pr->user, pr->ev_done, 0));
+    CUDA_TRY(cudaStreamSynchronize(pr->work));
+    return CCX_OK;
+}
+
+// Validate, sort by (i, j), drop zero weights, store and upload with CSR.
+ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const std::vector<int>& ej_in,
+                         const std::vector<double>& w_in) {
+    const int64_t n = pr->n;
+    const size_t m0 = ei_in.size();
+    std::vector<size_t> order;
+    order.reserve(m0);
+    for (size_t e = 0; e < m0; ++e) {
+        const int64_t a = ei_in[e], b = ej_in[e];
+        const double wt = w_in[e];
+        if (a < 0 || b < 0 || a >= n || b >= n)
+            return fail(CCX_EINVAL, "edge %zu: index out of range [0, %lld)", e, (long long)n);
+        if (a >= b) return fail(CCX_EINVAL, "edge %zu: need ei < ej (got %lld, %lld)", e, (long long)a, (long long)b);
+        if (!std::isfinite(wt) || wt < 0.0) return fail(CCX_EINVAL, "edge %zu: weight must be finite and >= 0", e);
+        if (wt > 0.0) order.push_back(e);
+    }
+    std::sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        return ei_in[x] != ei_in[y] ? ei_in[x] < ei_in[y] : ej_in[x] < ej_in[y];
+    });
+    for (size_t q = 1; q < order.size(); ++q)
+        if (ei_in[order[q]] == ei_in[order[q - 1]] && ej_in[order[q]] == ej_in[order[q - 1]])
+            return fail(CCX_EINVAL, "duplicate edge (%d, %d)", ei_in[order[q]], ej_in[order[q]]);
+    const int m = (int)order.size();
+    pr->ei.resize(m);
+    pr->ej.resize(m);
+    pr->w.resize(m);
+    double s2 = 0.0;
+    for (int q = 0; q < m; ++q) {
+        pr->ei[q] = ei_in[order[q]];
+        pr->ej[q] = ej_in[order[q]];
+        pr->w[q] = w_in[order[q]];
+        s2 += pr->w[q] * pr->w[q];
+    }
+    pr->nw = std::sqrt(s2);
+    // CSR over both directions; each row lists its neighbours by increasing index
+    std::vector<int> deg(n, 0);
+    for (int q = 0; q < m; ++q) {
+        deg[pr->ei[q]]++;
+        deg[pr->ej[q]]++;
+    }
+    std::vector<int> rowptr(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
+    pr->deg_max = n > 0 ? *std::max_element(deg.begin(), deg.end()) : 0;
+    std::vector<std::pair<int, int>> ent(2 * (size_t)m);
+    std::vector<int> fillp(rowptr.begin(), rowptr.end() - 1);
+    for (int q = 0; q < m; ++q) {
+        ent[fillp[pr->ei[q]]++] = {pr->ej[q], q};
+        ent[fillp[pr->ej[q]]++] = {pr->ei[q], q};
+    }
+    std::vector<int> col(2 * (size_t)m), eid(2 * (size_t)m);
+    for (int64_t i = 0; i < n; ++i) {
+        std::sort(ent.begin() + rowptr[i], ent.begin() + rowptr[i + 1]);
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            col[k] = ent[k].first;
+            eid[k] = ent[k].second;
+        }
+    }
+    free_path(pr);
+    free_edges(pr);
+    CUDA_TRY(dalloc(&pr->d_ei, m));
+    CUDA_TRY(dalloc(&pr->d_ej, m));
+    CUDA_TRY(dalloc(&pr->d_w, m));
+    CUDA_TRY(dalloc(&pr->d_rowptr, n + 1));
+    CUDA_TRY(dalloc(&pr->d_col, 2 * (size_t)m));
+    CUDA_TRY(dalloc(&pr->d_eid, 2 * (size_t)m));
+    if (m > 0) {
+        CUDA_TRY(cudaMemcpy(pr->d_ei, pr->ei.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(pr->d_ej, pr->ej.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(pr->d_w, pr->w.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(pr->d_col, col.data(), sizeof(int) * 2 * m, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(pr->d_eid, eid.data(), sizeof(int) * 2 * m, cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(cudaMemcpy(pr->d_rowptr, rowptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    return CCX_OK;
+}
+
+template <typename R>
+IterParams<R> make_params(ccx_problem* pr) {
+    IterParams<R> P{};
+    P.X = std::is_same<R, double>::value ? reinterpret_cast<const R*>(pr->Xd) : reinterpret_cast<const R*>(pr->Xf);
+    P.mask = pr->has_mask ? pr->maskbits : nullptr;
+    for (int k = 0; k < 2; ++k) {
+        P.Ahi[k] = reinterpret_cast<R*>(pr->A[k]);
+        P.Alo[k] = pr->Alo[k];
+        P.Dl[k] = reinterpret_cast<R*>(pr->Dl[k]);
+        P.t[k] = reinterpret_cast<R*>(pr->t[k]);
+    }
+    P.Q = reinterpret_cast<R*>(pr->Q);
+    P.Em = reinterpret_cast<R*>(pr->Em);
+    P.rowptr = pr->d_rowptr;
+    P.col = pr->d_col;
+    P.eid = pr->d_eid;
+    P.ei = pr->d_ei;
+    P.ej = pr->d_ej;
+    P.w = pr->d_w;
+    P.Pnb = pr->Pnb;
+    P.Ps = pr->Ps;
+    P.nb = pr->nb;
+    P.fused = pr->fused;
+    P.Rf = pr->Rf;
+    P.st = pr->st;
+    P.n = (int)pr->n;
+    P.ld = pr->ld;
+    P.ldw = pr->ldw;
+    P.m = (int)pr->ei.size();
+    P.nslices = pr->nslices;
+    P.G = pr->G;
+    return P;
+}
+
+ccx_status check_limits(ccx_problem* pr) {
+    const int m = (int)pr->ei.size();
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pr->device));
+    const size_t need = pd_slice_smem_bytes((int)pr->n, m, pr->precision == CCX_FP64);
+    if (need + 2048 > (size_t)optin)
+        return fail(CCX_EUNSUPPORTED,
+                    "n = %lld cases and %d edges need %zu bytes of shared memory per block (a column slice of "
+                    "all rows, %d bytes per row, plus 8 bytes per edge); the device allows %d",
+                    (long long)pr->n, m, need, pr->precision == CCX_FP64 ? 4 * kSliceCols * 8 : 6 * kSliceCols * 4,
+                    optin);
+    return CCX_OK;
+}
+
+ccx_status ensure_path(ccx_problem* pr) {
+    if (pr->path_ready) return CCX_OK;
+    const bool fp64 = pr->precision == CCX_FP64;
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    const size_t nl = (size_t)pr->n * pr->ld;
+    const int m = (int)pr->ei.size();
+    pr->nslices = (int)((pr->p + kSliceCols - 1) / kSliceCols);
+    pr->G = std::min(pr->nslices, pr->num_sms);
+    for (int k = 0; k < 2; ++k) {
+        CUDA_TRY(cudaMalloc(&pr->A[k], es * nl));
+        CUDA_TRY(cudaMalloc(&pr->Dl[k], es * nl));
+        if (!fp64) CUDA_TRY(dalloc(&pr->Alo[k], nl));
+        CUDA_TRY(cudaMalloc(&pr->t[k], es * std::max(m, 1)));
+    }
+    if (pr->has_mask) {
+        CUDA_TRY(cudaMalloc(&pr->Q, es * nl));
+        CUDA_TRY(cudaMalloc(&pr->Em, es * nl));
+    }
+    CUDA_TRY(dalloc(&pr->Pnb, (size_t)pr->G * std::max(m, 1)));
+    CUDA_TRY(dalloc(&pr->Ps, (size_t)pr->G * kNumScalarPartials));
+    CUDA_TRY(dalloc(&pr->nb, m));
+    CUDA_TRY(dalloc(&pr->fused, m));
+    CUDA_TRY(dalloc(&pr->Rf, 2 * 128));
+    CUDA_TRY(dalloc(&pr->st, 1));
+    CUDA_TRY(cudaMallocHost(&pr->st_host, 2 * sizeof(PdState)));
+    CUDA_TRY(dalloc(&pr->Ustage, (size_t)pr->n * pr->p));
+    CUDA_TRY(dalloc(&pr->Lstage, pr->n));
+    CUDA_TRY(dalloc(&pr->cc_scratch, pr->n));
+    CUDA_TRY(dalloc(&pr->d_ncl, 1));
+    CUDA_TRY(cudaMallocHost(&pr->h_ncl, sizeof(int)));
+    CUDA_TRY(cudaMemsetAsync(pr->st, 0, sizeof(PdState), pr->work));
+    pr->path_ready = true;
+    pr->path_started = false;
+    return CCX_OK;
+}
+
+ccx_status build_graph(ccx_problem* pr, int chunk) {
+    if (pr->graph && pr->graph_chunk == chunk) return CCX_OK;
+    if (pr->graph) {
+        cudaGraphExecDestroy(pr->graph);
+        pr->graph = nullptr;
+    }
+    // one launch outside capture sets the kernels' shared-memory attributes
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(pr->work, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < chunk && err == cudaSuccess; ++k) {
+        if (pr->precision == CCX_FP64) err = launch_pd_iteration<double>(make_params<double>(pr), pr->work);
+        else err = launch_pd_iteration<float>(make_params<float>(pr), pr->work);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(pr->work, &g);
+    g_launches.fetch_sub(2ULL * (unsigned long long)chunk, std::memory_order_relaxed);  // captured, not launched
+    if (err != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(CCX_ECUDA, "capturing the iteration graph failed: %s",
+                    cudaGetErrorString(err != cudaSuccess ? err : e2));
+    }
+    err = cudaGraphInstantiate(&pr->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return fail(CCX_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(err));
+    pr->graph_chunk = chunk;
+    return CCX_OK;
+}
+
+template <typename R>
+ccx_status run_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts& o, float* U_out,
+                    int32_t* labels_out, ccx_gamma_stats* stats) {
+    IterParams<R> P = make_params<R>(pr);
+    if (!pr->path_started) {
+        const R* Y0 = std::is_same<R, double>::value ? reinterpret_cast<const R*>(pr->Y0d)
+                                                      : reinterpret_cast<const R*>(pr->Y0f);
+        CUDA_TRY(launch_pd_init<R>(P, Y0, pr->work));
+        pr->path_started = true;
+    }
+    // The first launch of each kernel variant raises its shared-memory limit,
+    // which must not happen under capture: launch once on a finished state
+    // (done = 1, so every kernel returns at once) before capturing.
+    if (!pr->graph) CUDA_TRY(launch_pd_iteration<R>(P, pr->work));
+    {
+        ccx_status s = build_graph(pr, o.chunk);
+        if (s != CCX_OK) return s;
+    }
+    const bool u_dev = is_device_ptr(U_out);
+    const bool l_dev = is_device_ptr(labels_out);
+    bool all_conv = true;
+    for (int g = 0; g < n_gamma; ++g) {
+        const auto t0 = std::chrono::steady_clock::now();
+        const double gamma = gammas[g];
+        double rho = o.rho_scale * (pr->nyc + gamma * pr->nw);
+        if (!(rho > 0.0)) rho = o.rho_scale;
+        double eps = (o.eps_rel * pr->nyc) * (o.eps_rel * pr->nyc);
+        if (!(eps > 0.0)) eps = o.eps_rel * o.eps_rel;
+        const double unit = std::is_same<R, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const double scale_floor = 64.0 * unit * pr->ny0;
+        CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, o.tol, o.max_iter, o.accelerate, scale_floor,
+                                          pr->work));
+        // chunks of iterations; one chunk stays queued ahead of the host check
+        int launched = 0, checked = 0;
+        PdState final{};
+        for (;;) {
+            CUDA_TRY(cudaGraphLaunch(pr->graph, pr->work));
+            count_launches(2ULL * (unsigned long long)pr->graph_chunk);
+            CUDA_TRY(cudaMemcpyAsync(&pr->st_host[launched & 1], pr->st, sizeof(PdState), cudaMemcpyDeviceToHost,
+                                     pr->work));
+            CUDA_TRY(cudaEventRecord(pr->ev_chunk[launched & 1], pr->work));
+            ++launched;
+            if (launched - checked < 2) continue;
+            CUDA_TRY(cudaEventSynchronize(pr->ev_chunk[checked & 1]));
+            final = pr->st_host[checked & 1];
+            ++checked;
+            if (final.done) break;
+        }
+        // the chunk queued behind the finished one returns at once; wait for it
+        CUDA_TRY(cudaEventSynchronize(pr->ev_chunk[checked & 1]));
+        if (final.converged == 0) all_conv = false;
+        // outputs of this gamma
+        if (U_out) {
+            float* dst = U_out + (size_t)g * pr->n * pr->ld_in;
+            if (u_dev) {
+                CUDA_TRY(launch_pd_finalize<R>(P, dst, pr->ld_in, (int)pr->p, pr->work));
+            } else {
+                CUDA_TRY(launch_pd_finalize<R>(P, pr->Ustage, pr->p, (int)pr->p, pr->work));
+                CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(float) * pr->ld_in, pr->Ustage, sizeof(float) * pr->p,
+                                           sizeof(float) * pr->p, pr->n, cudaMemcpyDeviceToHost, pr->work));
+            }
+        }
+        int* ldst = (labels_out && l_dev) ? labels_out + (size_t)g * pr->n : pr->Lstage;
+        CUDA_TRY(launch_fused_labels((int)pr->n, P.m, pr->d_ei, pr->d_ej, pr->fused, ldst, pr->d_ncl,
+                                     pr->cc_scratch, pr->work));
+        if (labels_out && !l_dev)
+            CUDA_TRY(cudaMemcpyAsync(labels_out + (size_t)g * pr->n, pr->Lstage, sizeof(int) * pr->n,
+                                     cudaMemcpyDeviceToHost, pr->work));
+        CUDA_TRY(cudaMemcpyAsync(pr->h_ncl, pr->d_ncl, sizeof(int), cudaMemcpyDeviceToHost, pr->work));
+        CUDA_TRY(cudaStreamSynchronize(pr->work));
+        if (stats) {
+            ccx_gamma_stats& S = stats[g];
+            S.iters = final.iter;
+            S.converged = final.converged;
+            S.n_fused = std::max(final.n_fused, 0);
+            S.n_clusters = *pr->h_ncl;
+            S.gamma = gamma;
+            S.rho = rho;
+            S.eps = eps;
+            S.d_final = final.d_last;
+            S.err_est = final.err_est;
+            S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+    }
+    return all_conv ? CCX_OK : fail(CCX_ENOTCONV, "max_iter reached before convergence for some gamma");
+}
+
+}  // namespace
+
+extern "C" {
+
+void ccx_opts_default(ccx_opts* o) {
+    if (!o) return;
+    o->rho_scale = 2.0;
+    o->eps_rel = 1e-3;
+    o->tol = 1e-6;
+    o->max_iter = 200000;
+    o->accelerate = 1;
+    o->chunk = 64;
+}
+
+const char* ccx_last_error(void) { return g_err.c_str(); }
+
+const char* ccx_version(void) { return "ccx 0.1 (sm_103a)"; }
+
+ccx_status ccx_problem_create(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld, int precision,
+                              void* stream, ccx_problem** out) {
+    g_err.clear();
+    if (!out) return fail(CCX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!X) return fail(CCX_EINVAL, "X is NULL");
+    if (n < 1 || p < 1) return fail(CCX_EINVAL, "need n >= 1 and p >= 1 (got %lld, %lld)", (long long)n, (long long)p);
+    if (ld < p) return fail(CCX_EINVAL, "ld (%lld) < p (%lld)", (long long)ld, (long long)p);
+    if (precision != CCX_FP32 && precision != CCX_FP64) return fail(CCX_EINVAL, "precision must be CCX_FP32 or CCX_FP64");
+    if (n > (int64_t)1 << 30 || p > (int64_t)1 << 30) return fail(CCX_EINVAL, "n or p too large");
+    ccx_problem* pr = new ccx_problem();
+    pr->precision = precision;
+    pr->n = n;
+    pr->p = p;
+    pr->ld_in = ld;
+    pr->ld = (int)((p + 31) / 32 * 32);
+    pr->ldw = pr->ld / 32;
+    pr->has_mask = mask != nullptr;
+    pr->user = reinterpret_cast<cudaStream_t>(stream);
+    auto bail = [&](ccx_status s) {
+        free_all(pr);
+        delete pr;
+        return s;
+    };
+#define TRY(expr)                                                                                  \
+    do {                                                                                           \
+        cudaError_t _e = (expr);                                                                   \
+        if (_e != cudaSuccess)                                                                     \
+            return bail(fail(_e == cudaErrorMemoryAllocation ? CCX_ENOMEM : CCX_ECUDA, "%s: %s", #expr, \
+                             cudaGetErrorString(_e)));                                             \
+    } while (0)
+    TRY(cudaGetDevice(&pr->device));
+    TRY(cudaDeviceGetAttribute(&pr->num_sms, cudaDevAttrMultiProcessorCount, pr->device));
+    TRY(cudaStreamCreateWithFlags(&pr->work, cudaStreamNonBlocking));
+    TRY(cudaEventCreateWithFlags(&pr->ev_user, cudaEventDisableTiming));
+    TRY(cudaEventCreateWithFlags(&pr->ev_done, cudaEventDisableTiming));
+    TRY(cudaEventCreateWithFlags(&pr->ev_chunk[0], cudaEventDisableTiming));
+    TRY(cudaEventCreateWithFlags(&pr->ev_chunk[1], cudaEventDisableTiming));
+    TRY(cudaEventRecord(pr->ev_user, pr->user));
+    TRY(cudaStreamWaitEvent(pr->work, pr->ev_user, 0));
+    const size_t nl = (size_t)n * pr->ld;
+    TRY(dalloc(&pr->Xf, nl));
+    if (precision == CCX_FP64) TRY(dalloc(&pr->Xd, nl));
+    if (mask) TRY(dalloc(&pr->maskbits, (size_t)n * pr->ldw));
+    TRY(dalloc(&pr->colmean, 2 * (size_t)pr->ld));
+    TRY(dalloc(&pr->Y0f, nl));
+    if (precision == CCX_FP64) TRY(dalloc(&pr->Y0d, nl));
+    TRY(dalloc(&pr->d_ss, 1));
+    // stage caller arrays on the device
+    const float* Xsrc = X;
+    const uint8_t* Msrc = mask;
+    float* Xtmp = nullptr;
+    uint8_t* Mtmp = nullptr;
+    int* bad = nullptr;
+    if (!is_device_ptr(X)) {
+        TRY(dalloc(&Xtmp, (size_t)n * ld));
+        TRY(cudaMemcpyAsync(Xtmp, X, sizeof(float) * (size_t)n * ld, cudaMemcpyHostToDevice, pr->work));
+        Xsrc = Xtmp;
+    }
+    if (mask && !is_device_ptr(mask)) {
+        TRY(dalloc(&Mtmp, (size_t)n * ld));
+        TRY(cudaMemcpyAsync(Mtmp, mask, (size_t)n * ld, cudaMemcpyHostToDevice, pr->work));
+        Msrc = Mtmp;
+    }
+    TRY(dalloc(&bad, 2));
+    TRY(cudaMemsetAsync(bad, 0, 2 * sizeof(int), pr->work));
+    TRY(launch_pack_input(Xsrc, Msrc, n, p, ld, pr->Xf, pr->Xd, pr->maskbits, pr->ld, pr->ldw, bad, pr->work));
+    TRY(launch_fill_missing(pr->Xf, pr->Xd, pr->maskbits, (int)n, (int)p, pr->ld, pr->ldw, pr->colmean, pr->Y0f,
+                            pr->Y0d, pr->d_ss, pr->work));
+    int hbad[2] = {0, 0};
+    double ss = 0.0;
+    TRY(cudaMemcpyAsync(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, pr->work));
+    TRY(cudaMemcpyAsync(&ss, pr->d_ss, sizeof(double), cudaMemcpyDeviceToHost, pr->work));
+    TRY(cudaStreamSynchronize(pr->work));
+    cudaFree(Xtmp);
+    cudaFree(Mtmp);
+    cudaFree(bad);
+    if (hbad[0] > 0) return bail(fail(CCX_EINVAL, "%d observed entries of X are not finite", hbad[0]));
+    if (hbad[1] > 0) return bail(fail(CCX_EINVAL, "%d rows have no observed entry", hbad[1]));
+    pr->nyc = std::sqrt(ss);
+    {
+        std::vector<double> cm(p);
+        TRY(cudaMemcpy(cm.data(), pr->colmean, sizeof(double) * p, cudaMemcpyDeviceToHost));
+        double s0 = 0.0;
+        for (int64_t c = 0; c < p; ++c) s0 += cm[c] * cm[c];
+        pr->ny0 = std::sqrt(ss + (double)n * s0);   // ||Y_0||^2 = ||Y_c||^2 + n ||mean||^2
+    }
+    // an empty edge set until the caller sets or builds one
+    {
+        std::vector<int> e0;
+        std::vector<double> w0;
+        ccx_status s = install_edges(pr, e0, e0, w0);
+        if (s != CCX_OK) return bail(s);
+    }
+#undef TRY
+    *out = pr;
+    return CCX_OK;
+}
+
+ccx_status ccx_set_edges(ccx_problem* pr, int64_t n_edges, const int32_t* ei, const int32_t* ej, const double* w) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    if (n_edges < 0) return fail(CCX_EINVAL, "n_edges < 0");
+    if (n_edges > 0 && (!ei || !ej || !w)) return fail(CCX_EINVAL, "edge arrays are NULL");
+    CUDA_TRY(cudaSetDevice(pr->device));
+    std::vector<int> a(ei, ei + n_edges), b(ej, ej + n_edges);
+    std::vector<double> c(w, w + n_edges);
+    return install_edges(pr, a, b, c);
+}
+
+ccx_status ccx_build_knn(ccx_problem* pr, const ccx_knn_rule* rule) {
+    g_err.clear();
+    if (!pr || !rule) return fail(CCX_EINVAL, "NULL argument");
+    if (rule->k < 1) return fail(CCX_EINVAL, "k must be >= 1");
+    if (!rule->phi_auto && (!std::isfinite(rule->phi) || rule->phi < 0.0))
+        return fail(CCX_EINVAL, "phi must be finite and >= 0");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    knn_set_exact_rows(pr->Xf, pr->has_mask ? pr->maskbits : nullptr, pr->colmean, pr->ldw);
+    KnnResult res;
+    std::string err;
+    cudaError_t e = knn_build(pr->Y0f, (int)pr->n, (int)pr->p, pr->ld, rule->k, rule->phi, rule->phi_auto,
+                              rule->normalize, pr->work, &res, &err);
+    if (e == cudaErrorNotSupported) return fail(CCX_EUNSUPPORTED, "%s", err.c_str());
+    if (e != cudaSuccess) return fail(CCX_ECUDA, "kNN build failed: %s", cudaGetErrorString(e));
+    s = install_edges(pr, res.ei, res.ej, res.w);
+    if (s != CCX_OK) return s;
+    return leave(pr);
+}
+
+ccx_status ccx_get_edges(const ccx_problem* pr, int64_t* n_edges, int32_t* ei, int32_t* ej, double* w) {
+    g_err.clear();
+    if (!pr || !n_edges) return fail(CCX_EINVAL, "NULL argument");
+    const int64_t m = (int64_t)pr->ei.size();
+    if (!ei) {
+        *n_edges = m;
+        return CCX_OK;
+    }
+    if (*n_edges < m) return fail(CCX_EINVAL, "capacity %lld < %lld edges", (long long)*n_edges, (long long)m);
+    std::copy(pr->ei.begin(), pr->ei.end(), ei);
+    if (ej) std::copy(pr->ej.begin(), pr->ej.end(), ej);
+    if (w) std::copy(pr->w.begin(), pr->w.end(), w);
+    *n_edges = m;
+    return CCX_OK;
+}
+
+ccx_status ccx_fusion_scale(const ccx_problem* pr_c, double* gamma0) {
+    g_err.clear();
+    ccx_problem* pr = const_cast<ccx_problem*>(pr_c);
+    if (!pr || !gamma0) return fail(CCX_EINVAL, "NULL argument");
+    const int m = (int)pr->ei.size();
+    if (m == 0) return fail(CCX_EINVAL, "no edges");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    double* d2 = nullptr;
+    CUDA_TRY(dalloc(&d2, m));
+    cudaError_t e = edge_distances(pr->Y0f, (int)pr->n, (int)pr->p, pr->ld, pr->d_ei, pr->d_ej, m, d2, pr->work);
+    std::vector<double> h(m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d2, sizeof(double) * m, cudaMemcpyDeviceToHost, pr->work);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pr->work);
+    cudaFree(d2);
+    if (e != cudaSuccess) return fail(CCX_ECUDA, "fusion scale: %s", cudaGetErrorString(e));
+    for (int q = 0; q < m; ++q) h[q] = std::sqrt(h[q]) / (2.0 * pr->w[q]);
+    std::sort(h.begin(), h.end());
+    *gamma0 = (m % 2) ? h[m / 2] : 0.5 * (h[m / 2 - 1] + h[m / 2]);
+    return leave(pr);
+}
+
+ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts, float* U_out,
+                          int32_t* labels_out, ccx_gamma_stats* stats) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    if (n_gamma < 0) return fail(CCX_EINVAL, "n_gamma < 0");
+    if (n_gamma > 0 && !gammas) return fail(CCX_EINVAL, "gammas is NULL");
+    for (int g = 0; g < n_gamma; ++g)
+        if (!std::isfinite(gammas[g]) || gammas[g] < 0.0)
+            return fail(CCX_EINVAL, "gammas[%d] must be finite and >= 0", g);
+    ccx_opts o;
+    ccx_opts_default(&o);
+    if (pr->precision == CCX_FP64) o.tol = 1e-10;
+    if (opts) o = *opts;
+    if (!(o.rho_scale > 0.0) || !std::isfinite(o.rho_scale)) return fail(CCX_EINVAL, "rho_scale must be > 0");
+    if (!(o.eps_rel > 0.0) || !std::isfinite(o.eps_rel)) return fail(CCX_EINVAL, "eps_rel must be > 0");
+    if (!(o.tol > 0.0)) return fail(CCX_EINVAL, "tol must be > 0");
+    if (o.max_iter < 1) return fail(CCX_EINVAL, "max_iter must be >= 1");
+    if (o.chunk < 1 || o.chunk > 4096) return fail(CCX_EINVAL, "chunk must be in [1, 4096]");
+    ccx_status s = check_limits(pr);
+    if (s != CCX_OK) return s;
+    s = enter(pr);
+    if (s != CCX_OK) return s;
+    s = ensure_path(pr);
+    if (s != CCX_OK) return s;
+    ccx_status r = pr->precision == CCX_FP64 ? run_path<double>(pr, gammas, n_gamma, o, U_out, labels_out, stats)
+                                             : run_path<float>(pr, gammas, n_gamma, o, U_out, labels_out, stats);
+    std::string keep = g_err;
+    ccx_status l = leave(pr);
+    if (r != CCX_OK) {
+        g_err = keep;
+        return r;
+    }
+    return l;
+}
+
+ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts, double* slice_ms,
+                               double* reduce_ms) {
+    g_err.clear();
+    if (!pr || !slice_ms || !reduce_ms) return fail(CCX_EINVAL, "NULL argument");
+    if (!std::isfinite(gamma) || gamma < 0.0) return fail(CCX_EINVAL, "gamma must be finite and >= 0");
+    if (n_iter < 1) return fail(CCX_EINVAL, "n_iter must be >= 1");
+    ccx_opts o;
+    ccx_opts_default(&o);
+    if (opts) o = *opts;
+    ccx_status s = check_limits(pr);
+    if (s != CCX_OK) return s;
+    s = enter(pr);
+    if (s != CCX_OK) return s;
+    s = ensure_path(pr);
+    if (s != CCX_OK) return s;
+    const bool fp64 = pr->precision == CCX_FP64;
+    double rho = o.rho_scale * (pr->nyc + gamma * pr->nw);
+    if (!(rho > 0.0)) rho = o.rho_scale;
+    double eps = (o.eps_rel * pr->nyc) * (o.eps_rel * pr->nyc);
+    if (!(eps > 0.0)) eps = o.eps_rel * o.eps_rel;
+    std::vector<cudaEvent_t> ev(3 * (size_t)n_iter);
+    for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+    auto body = [&](auto tag) -> ccx_status {
+        using R = decltype(tag);
+        IterParams<R> P = make_params<R>(pr);
+        if (!pr->path_started) {
+            const R* Y0 = fp64 ? reinterpret_cast<const R*>(pr->Y0d) : reinterpret_cast<const R*>(pr->Y0f);
+            CUDA_TRY(launch_pd_init<R>(P, Y0, pr->work));
+            pr->path_started = true;
+        }
+        // tol < 0: neither stopping rule fires; max_iter leaves room for all iterations
+        CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, -1.0, n_iter + 1, o.accelerate, 0.0, pr->work));
+        for (int k = 0; k < n_iter; ++k) {
+            CUDA_TRY(cudaEventRecord(ev[3 * k], pr->work));
+            CUDA_TRY(launch_pd_slice<R>(P, pr->work));
+            CUDA_TRY(cudaEventRecord(ev[3 * k + 1], pr->work));
+            CUDA_TRY(launch_pd_reduce<R>(P, pr->work));
+            CUDA_TRY(cudaEventRecord(ev[3 * k + 2], pr->work));
+        }
+        CUDA_TRY(cudaStreamSynchronize(pr->work));
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < n_iter; ++k) {
+            float t1 = 0.f, t2 = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t1, ev[3 * k], ev[3 * k + 1]));
+            CUDA_TRY(cudaEventElapsedTime(&t2, ev[3 * k + 1], ev[3 * k + 2]));
+            a += t1;
+            b += t2;
+        }
+        *slice_ms = a / n_iter;
+        *reduce_ms = b / n_iter;
+        return CCX_OK;
+    };
+    s = fp64 ? body(double{}) : body(float{});
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (s != CCX_OK) return s;
+    return leave(pr);
+}
+
+uint64_t ccx_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+ccx_status ccx_reset_path(ccx_problem* pr) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    pr->path_started = false;
+    return CCX_OK;
+}
+
+ccx_status ccx_problem_destroy(ccx_problem* pr) {
+    g_err.clear();
+    if (!pr) return CCX_OK;
+    cudaSetDevice(pr->device);
+    cudaStreamSynchronize(pr->work);
+    free_all(pr);
+    delete pr;
+    return CCX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Internal declarations of the ccx library (not part of the C ABI).
+//
+// Data layout on the device (one problem):
+//   * every n x p matrix is row-major with an internal row stride ld that is
+//     p rounded up to a multiple of 32 elements; padding columns hold 0 and
+//     stay 0 through every kernel;
+//   * the observation mask is bit-packed, n rows of ld/32 words, bit = 1 for
+//     observed (padding columns are marked observed);
+//   * the projection A of the MM iteration is kept in float-float (hi + lo
+//     float arrays) for the FP32 path and in double for the FP64 path; all
+//     other per-entry quantities are in the path's real type R.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ccx.h"
+
+namespace ccx {
+
+constexpr int kSliceThreads = 512;   // threads of the fused iteration kernel
+constexpr int kSliceCols = 4;        // columns per staged slice (one 16-byte vector for float)
+constexpr int kReduceThreads = 256;
+constexpr int kConvWindow = 64;      // iterations per convergence window
+constexpr int kRateWindows = 8;      // windows spanned by the contraction-rate estimate
+constexpr int kNumScalarPartials = 8;
+constexpr double kStallSteps = 128.0;  // error bound, in steps, once steps are at the rounding level
+constexpr double kNoiseFactor = 32.0;  // steps within this factor of the rounding noise: no progress possible
+constexpr int kNoiseWindows = 4;       // consecutive such windows before stopping
+
+// Scalar partial slots written by each CTA of the iteration kernel.
+enum : int {
+    kPsUA = 0,     // ||U_y - A_m||^2
+    kPsVB = 1,     // ||V_y - B_m||^2
+    kPsRestart = 2,// <a_start - A_m, A_m - A_{m-1}> (restart test)
+    kPsStep = 3,   // ||A_m - A_{m-1}||^2
+    kPsNormA = 4,  // ||A_m||^2
+    kPsNoise = 5,  // sum of ((|U_y - A_start| + |G|) / (1 + deg))^2: rounding scale of the step
+    kPsDelta = 6,  // ||A_m - A_start||^2: residual of the map at the extrapolated point
+};
+
+// Device-resident scalar state of the MM iteration of one problem.  Written
+// by the host only between gammas (through pd_begin_gamma) and otherwise by
+// the last block of pd_reduce_kernel.
+struct PdState {
+    double alpha1;        // alpha_{m-1} = d_{m-1} / (d_{m-1} + rho_{m-1})
+    double alpha2;        // alpha_{m-2}
+    double beta;          // extrapolation weight used by the next iteration
+    double gamma, rho, eps, tol;
+    double d_last;
+    double blk_max, err_est, a_norm;
+    double scale_floor;   // lower bound of the error scale (rounding level of the data)
+    double noise_max;     // window maximum of the rounding-noise scale of the step
+    double dmax;          // window maximum of ||A_m - A_start|| (the map's residual)
+    double ring[kRateWindows];  // recent window maxima of that residual
+    int ring_len;
+    int floor_hits;       // consecutive windows with steps at the rounding level
+    unsigned long long fused_hash;
+    int k_mom;
+    int accelerate;
+    int par;              // slot parity: input slots of the next iteration
+    int iter;             // iterations done on the current gamma
+    int max_iter;
+    int done;             // current gamma finished
+    int converged;        // 1: tolerance met, 2: stopped at the rounding floor
+    int hits;             // consecutive windows that met the tolerance
+    int n_fused;
+    int fused_stable;     // iterations since the fused set last changed
+    unsigned int counter; // arrival counter of the reduce kernel's blocks
+    int pad_;
+};
+
+template <typename R>
+struct IterParams {
+    const R* X;                 // n x ld data (observed entries; 0 elsewhere)
+    const uint32_t* mask;       // n x ldw bits, or nullptr (all observed)
+    R* Ahi[2];                  // A slots (hi part, or the double value)
+    float* Alo[2];              // A slots (lo part; FP32 path only)
+    R* Dl[2];                   // velocity slots Delta = A_m - A_{m-1}
+    R* Q;                       // missing entries: U_y - A of the last iteration
+    R* Em;                      // missing entries: U - A_prev of the last iteration
+    R* t[2];                    // per-edge t = 1 - s slots
+    const int* rowptr;          // CSR over both directions, n + 1
+    const int* col;             // neighbour of each CSR entry
+    const int* eid;             // edge id of each CSR entry
+    const int* ei;              // edge endpoints, i < j
+    const int* ej;
+    const double* w;            // edge weights
+    double* Pnb;                // per-CTA per-edge partial ||b||^2, G x m
+    double* Ps;                 // per-CTA scalar partials, G x kNumScalarPartials
+    double* nb;                 // per-edge ||b_m|| of the last iteration
+    uint8_t* fused;             // per-edge fused flag of t_{m+1}
+    unsigned long long* Rf;     // per reduce-block fused count / hash
+    PdState* st;
+    int n, ld, ldw, m, nslices, G;
+};
+
+// ---------------------------------------------------------------- launchers
+// (defined in pd_kernels.cu; all asynchronous on `s`)
+template <typename R>
+cudaError_t launch_pd_init(const IterParams<R>& P, const R* Y0, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pd_begin_gamma(const IterParams<R>& P, double gamma, double rho, double eps, double tol,
+                                  int max_iter, int accelerate, double scale_floor, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pd_iteration(const IterParams<R>& P, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pd_slice(const IterParams<R>& P, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s);
+// library-wide count of kernel launches (incremented by every launcher)
+void count_launches(unsigned long long k);
+template <typename R>
+cudaError_t launch_pd_finalize(const IterParams<R>& P, float* U_out, int64_t ld_out, int p, cudaStream_t s);
+size_t pd_slice_smem_bytes(int n, int m, bool fp64);
+
+// data preparation (prep_kernels.cu)
+cudaError_t launch_pack_input(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld_in,
+                              float* Xf, double* Xd, uint32_t* maskbits, int ld, int ldw, int* bad_count,
+                              cudaStream_t s);
+cudaError_t launch_fill_missing(const float* Xf, const double* Xd, const uint32_t* maskbits, int n, int p,
+                                int ld, int ldw, double* colmean, float* Y0f, double* Y0d, double* ss,
+                                cudaStream_t s);
+
+// connected components of the fused edges (cc_kernels.cu)
+cudaError_t launch_fused_labels(int n, int m, const int* ei, const int* ej, const uint8_t* fused,
+                                int* labels, int* n_clusters, int* scratch, cudaStream_t s);
+
+// kNN weights (knn_kernels.cu)
+struct KnnResult {
+    std::vector<int> ei, ej;
+    std::vector<double> w, d2;
+    double phi = 0.0;
+};
+cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
+                      cudaStream_t s, KnnResult* out, std::string* err);
+cudaError_t edge_distances(const float* Y0f, int n, int p, int ld, const int* ei_d, const int* ej_d, int m,
+                           double* d2_d, cudaStream_t s);
+
+}  // namespace ccx

@@ -1,0 +1,375 @@
+// kNN union graph with Gaussian-kernel weights (Calibration of Weights, Eq. 8).
+//
+// 1. y_i = row i of Y_0 (missing entries at the observed column mean, in
+//    double); sq_i = ||y_i||^2 and nrm_i = ||y_i|| in double.
+// 2. Gram matrix G ~ Y Y^T of the float copy of Y_0 (gram_f32_kernel, or the
+//    tensor-core kernel in gram_tc.cu), giving approximate squared distances
+//    a_ij = sq_i + sq_j - 2 G_ij.
+// 3. Per row i (knn_row_kernel): with a rigorous per-pair bound
+//    |a_ij - d2_ij| <= b_ij, T = k-th smallest (a_ij + b_ij) bounds the true
+//    k-th smallest distance from above, so every true neighbour satisfies
+//    a_ij - b_ij <= T.  Those candidates get their distance recomputed
+//    exactly from the rows (double differences and sums in a fixed order),
+//    and the k smallest by (d2, j) are kept: ties go to the smaller index.
+// 4. The union i ~_k j, phi, the weights and the normalisation are formed on
+//    the host from the exact d2 (knn_build).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <numeric>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "ccx_internal.h"
+
+namespace ccx {
+
+// defined in gram_tc.cu: G = Y Y^T on the tensor cores; returns cudaErrorNotSupported
+// when the shape is outside the kernel's tiling, and the per-entry relative
+// input rounding it used through *unit.
+cudaError_t launch_gram_tc(const float* Y, int n, int p, int ld, float* G, double* unit, cudaStream_t s);
+
+namespace {
+
+constexpr int kRowThreads = 256;
+
+__global__ void row_norm_kernel(const float* __restrict__ Xf, const uint32_t* __restrict__ bits,
+                                const double* __restrict__ colmean, int n, int p, int ld, int ldw,
+                                double* __restrict__ sq) {
+    const int i = blockIdx.x;
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        const bool obs = bits ? ((bits[(size_t)i * ldw + (c >> 5)] >> (c & 31)) & 1u) : true;
+        const double y = obs ? (double)Xf[(size_t)i * ld + c] : colmean[c];
+        s += y * y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        sq[i] = t;
+    }
+}
+
+// Plain FP32 Gram, 64 x 64 tiles, 16 x 16 threads, 4 x 4 outputs each.
+__global__ void __launch_bounds__(256) gram_f32_kernel(const float* __restrict__ Y, int n, int p, int ld,
+                                                       float* __restrict__ G) {
+    __shared__ float sa[16][64 + 4];
+    __shared__ float sb[16][64 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < p; k0 += 16) {
+        for (int q = threadIdx.x; q < 64 * 16; q += 256) {
+            const int r = q >> 4, kk = q & 15;
+            const int gr = row0 + r, gc = col0 + r, gk = k0 + kk;
+            sa[kk][r] = (gr < n && gk < p) ? Y[(size_t)gr * ld + gk] : 0.f;
+            sb[kk][r] = (gc < n && gk < p) ? Y[(size_t)gc * ld + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = sa[kk][ty * 4 + u];
+                b[u] = sb[kk][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = row0 + ty * 4 + u, c = col0 + tx * 4 + v;
+            if (r < n && c < n) G[(size_t)r * n + c] = acc[u][v];
+        }
+}
+
+// bitonic sort of (key, idx) pairs in shared memory, ascending by (key, idx)
+__device__ void bitonic_sort(double* key, int* idx, int len_pow2) {
+    for (int size = 2; size <= len_pow2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < len_pow2; t += blockDim.x) {
+                const int partner = t ^ stride;
+                if (partner > t) {
+                    const bool up = ((t & size) == 0);
+                    const double ka = key[t], kb = key[partner];
+                    const int ia = idx[t], ib = idx[partner];
+                    const bool gt = (ka > kb) || (ka == kb && ia > ib);
+                    if (gt == up) {
+                        key[t] = kb;
+                        key[partner] = ka;
+                        idx[t] = ib;
+                        idx[partner] = ia;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRowThreads) knn_row_kernel(
+    const float* __restrict__ Xf, const uint32_t* __restrict__ bits, const double* __restrict__ colmean,
+    const double* __restrict__ sq, const float* __restrict__ G, double gunit, int use_all, int n, int p, int ld,
+    int ldw, int k, int npow2, int* __restrict__ nbr, double* __restrict__ nd2) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    double* key = reinterpret_cast<double*>(sm);          // npow2
+    double* av = key + npow2;                             // n: approx a_ij
+    double* bv = av + n;                                  // n: bound b_ij
+    int* idx = reinterpret_cast<int*>(bv + n);            // npow2
+    int* cand = idx + npow2;                              // n
+    __shared__ int ncand;
+    __shared__ double Tsh;
+    const int i = blockIdx.x;
+    const double sqi = sq[i], nri = sqrt(sq[i]);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        if (use_all) {
+            av[j] = 0.0;
+            bv[j] = 0.0;
+        } else {
+            const double a = sqi + sq[j] - 2.0 * (double)G[(size_t)i * n + j];
+            // |G_ij - <y_i, y_j>| <= gunit * ||y_i|| ||y_j||; d2 = sq_i + sq_j - 2 <y_i, y_j>
+            const double b = 2.0 * gunit * nri * sqrt(sq[j]) * (1.0 + 1e-9) + 1e-300;
+            av[j] = a;
+            bv[j] = b;
+        }
+    }
+    __syncthreads();
+    if (use_all) {
+        if (threadIdx.x == 0) Tsh = INFINITY;
+    } else {
+        for (int t = threadIdx.x; t < npow2; t += blockDim.x) {
+            key[t] = (t < n && t != i) ? av[t] + bv[t] : INFINITY;
+            idx[t] = t;
+        }
+        __syncthreads();
+        bitonic_sort(key, idx, npow2);
+        if (threadIdx.x == 0) Tsh = key[k - 1];
+    }
+    if (threadIdx.x == 0) ncand = 0;
+    __syncthreads();
+    const double T = Tsh;
+    // candidates: a - b <= T (order fixed later by the sort)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        if (j != i && (use_all || av[j] - bv[j] <= T)) {
+            const int slot = atomicAdd(&ncand, 1);
+            cand[slot] = j;
+        }
+    }
+    __syncthreads();
+    const int nc = ncand;
+    // exact distances, one warp per candidate, double throughout
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = wid; q < nc; q += nw) {
+        const int j = cand[q];
+        double s = 0.0;
+        for (int c = lane; c < p; c += 32) {
+            const uint32_t wi = bits ? bits[(size_t)i * ldw + (c >> 5)] : 0xffffffffu;
+            const uint32_t wj = bits ? bits[(size_t)j * ldw + (c >> 5)] : 0xffffffffu;
+            const double yi = ((wi >> (c & 31)) & 1u) ? (double)Xf[(size_t)i * ld + c] : colmean[c];
+            const double yj = ((wj >> (c & 31)) & 1u) ? (double)Xf[(size_t)j * ld + c] : colmean[c];
+            const double dd = yi - yj;
+            s += dd * dd;
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) av[j] = s;   // av now holds exact d2 for candidates
+    }
+    __syncthreads();
+    int cp2 = 1;
+    while (cp2 < nc) cp2 <<= 1;
+    for (int t = threadIdx.x; t < cp2; t += blockDim.x) {
+        if (t < nc) {
+            key[t] = av[cand[t]];
+            idx[t] = cand[t];
+        } else {
+            key[t] = INFINITY;
+            idx[t] = 0x7fffffff;
+        }
+    }
+    __syncthreads();
+    bitonic_sort(key, idx, cp2);
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        nbr[(size_t)i * k + r] = idx[r];
+        nd2[(size_t)i * k + r] = key[r];
+    }
+}
+
+__global__ void edge_d2_kernel(const float* __restrict__ Y, int p, int ld, const int* __restrict__ ei,
+                               const int* __restrict__ ej, int m, double* __restrict__ d2) {
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (e >= m) return;
+    const float* a = Y + (size_t)ei[e] * ld;
+    const float* b = Y + (size_t)ej[e] * ld;
+    double s = 0.0;
+    for (int c = lane; c < p; c += 32) {
+        const double dd = (double)a[c] - (double)b[c];
+        s += dd * dd;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) d2[e] = s;
+}
+
+}  // namespace
+
+cudaError_t edge_distances(const float* Y0f, int n, int p, int ld, const int* ei_d, const int* ej_d, int m,
+                           double* d2_d, cudaStream_t s) {
+    (void)n;
+    if (m == 0) return cudaSuccess;
+    count_launches(1);
+    edge_d2_kernel<<<(m + 7) / 8, 256, 0, s>>>(Y0f, p, ld, ei_d, ej_d, m, d2_d);
+    return cudaGetLastError();
+}
+
+// Y0f: float Y_0 (device, n x ld); the knn needs the exact rows as well, which
+// are Xf + mask + colmean.  Those are passed through knn_args (set by the API).
+struct KnnDeviceArgs {
+    const float* Xf;
+    const uint32_t* bits;
+    const double* colmean;
+    int ldw;
+};
+static thread_local KnnDeviceArgs g_knn_args;
+void knn_set_exact_rows(const float* Xf, const uint32_t* bits, const double* colmean, int ldw) {
+    g_knn_args = {Xf, bits, colmean, ldw};
+}
+
+cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
+                      cudaStream_t s, KnnResult* out, std::string* err) {
+    const KnnDeviceArgs ka = g_knn_args;
+    if (n > 4096) {
+        *err = "kNN build supports n <= 4096 in this build";
+        return cudaErrorNotSupported;
+    }
+    const int kk = std::min(k, n - 1);
+    out->ei.clear();
+    out->ej.clear();
+    out->w.clear();
+    out->d2.clear();
+    if (kk <= 0) return cudaSuccess;
+    const int use_all = (kk >= n - 1) ? 1 : 0;
+    cudaError_t e;
+    double* sq = nullptr;
+    float* G = nullptr;
+    int* nbr = nullptr;
+    double* nd2 = nullptr;
+    double gunit = 0.0;
+    auto cleanup = [&]() {
+        cudaFree(sq);
+        cudaFree(G);
+        cudaFree(nbr);
+        cudaFree(nd2);
+    };
+    if ((e = cudaMalloc(&sq, sizeof(double) * n)) != cudaSuccess) return cleanup(), e;
+    if ((e = cudaMalloc(&nbr, sizeof(int) * (size_t)n * kk)) != cudaSuccess) return cleanup(), e;
+    if ((e = cudaMalloc(&nd2, sizeof(double) * (size_t)n * kk)) != cudaSuccess) return cleanup(), e;
+    count_launches(1);
+    row_norm_kernel<<<n, 256, 0, s>>>(ka.Xf, ka.bits, ka.colmean, n, p, ld, ka.ldw, sq);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(), e;
+    if (!use_all) {
+        if ((e = cudaMalloc(&G, sizeof(float) * (size_t)n * n)) != cudaSuccess) return cleanup(), e;
+        e = launch_gram_tc(Y0f, n, p, ld, G, &gunit, s);
+        if (e == cudaErrorNotSupported) {
+            (void)cudaGetLastError();
+            dim3 grid((n + 63) / 64, (n + 63) / 64);
+            count_launches(1);
+            gram_f32_kernel<<<grid, 256, 0, s>>>(Y0f, n, p, ld, G);
+            e = cudaGetLastError();
+            // float inputs carry the float rounding of the filled missing entries
+            // (relative 2^-24) and FP32 accumulation over p terms
+            const double u = 1.0 / 16777216.0;
+            gunit = 2.0 * u + (double)(p + 2) * u;
+        }
+        if (e != cudaSuccess) return cleanup(), e;
+    }
+    int npow2 = 1;
+    while (npow2 < n) npow2 <<= 1;
+    const size_t smem = sizeof(double) * (size_t)(npow2 + 2 * n) + sizeof(int) * (size_t)(npow2 + n);
+    if ((e = cudaFuncSetAttribute(knn_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return cleanup(), e;
+    count_launches(1);
+    knn_row_kernel<<<n, kRowThreads, smem, s>>>(ka.Xf, ka.bits, ka.colmean, sq, G, gunit, use_all, n, p, ld, ka.ldw,
+                                                kk, npow2, nbr, nd2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(), e;
+    std::vector<int> hn((size_t)n * kk);
+    std::vector<double> hd((size_t)n * kk);
+    if ((e = cudaMemcpyAsync(hn.data(), nbr, sizeof(int) * hn.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cleanup(), e;
+    if ((e = cudaMemcpyAsync(hd.data(), nd2, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+        return cleanup(), e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(), e;
+    cleanup();
+    // union i ~_k j, sorted by (i, j)
+    std::vector<std::pair<long long, double>> pairs;
+    pairs.reserve(hn.size());
+    for (int i = 0; i < n; ++i)
+        for (int r = 0; r < kk; ++r) {
+            const int j = hn[(size_t)i * kk + r];
+            const int a = std::min(i, j), b = std::max(i, j);
+            pairs.push_back({(long long)a * n + b, hd[(size_t)i * kk + r]});
+        }
+    std::sort(pairs.begin(), pairs.end(),
+              [](const std::pair<long long, double>& x, const std::pair<long long, double>& y) {
+                  return x.first < y.first;
+              });
+    for (size_t q = 0; q < pairs.size(); ++q) {
+        if (q > 0 && pairs[q].first == pairs[q - 1].first) continue;
+        out->ei.push_back((int)(pairs[q].first / n));
+        out->ej.push_back((int)(pairs[q].first % n));
+        out->d2.push_back(pairs[q].second);
+    }
+    const size_t m = out->d2.size();
+    if (phi_auto) {
+        std::vector<double> t = out->d2;
+        std::sort(t.begin(), t.end());
+        double med = 0.0;
+        if (m > 0) med = (m % 2) ? t[m / 2] : 0.5 * (t[m / 2 - 1] + t[m / 2]);
+        phi = med > 0 ? 1.0 / med : 0.0;
+    }
+    out->phi = phi;
+    out->w.resize(m);
+    if (normalize && m > 0) {
+        const double dmin = *std::min_element(out->d2.begin(), out->d2.end());
+        double tot = 0.0;
+        for (size_t q = 0; q < m; ++q) {
+            out->w[q] = std::exp(-phi * (out->d2[q] - dmin));
+            tot += out->w[q];
+        }
+        for (size_t q = 0; q < m; ++q) out->w[q] /= tot;
+    } else {
+        for (size_t q = 0; q < m; ++q) out->w[q] = std::exp(-phi * out->d2[q]);
+    }
+    // drop exact zeros
+    size_t keep = 0;
+    for (size_t q = 0; q < m; ++q) {
+        if (out->w[q] > 0.0) {
+            out->ei[keep] = out->ei[q];
+            out->ej[keep] = out->ej[q];
+            out->d2[keep] = out->d2[q];
+            out->w[keep] = out->w[q];
+            ++keep;
+        }
+    }
+    out->ei.resize(keep);
+    out->ej.resize(keep);
+    out->d2.resize(keep);
+    out->w.resize(keep);
+    return cudaSuccess;
+}
+
+}  // namespace ccx

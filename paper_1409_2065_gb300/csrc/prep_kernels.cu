@@ -1,0 +1,168 @@
+// Input packing and the start matrix Y_0.
+//
+// pack_input: copies the caller's X (n x p floats, stride ld_in, already on
+// the device) into the internal padded layout (stride ld, padding = 0), sets
+// missing entries to 0, bit-packs the mask (padding marked observed) and
+// counts non-finite observed entries and rows without any observed entry.
+//
+// fill_missing: Y_0 = X with each missing entry replaced by its column's
+// observed mean (Methods, "Missing Data", start of the iteration; also the
+// fill used for the weights), and ||Y_c||_F^2, the squared Frobenius norm of
+// the column-centred Y_0, in double with a fixed summation order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "ccx_internal.h"
+
+namespace ccx {
+namespace {
+
+__global__ void pack_values_kernel(const float* __restrict__ X, const uint8_t* __restrict__ mask, int64_t n,
+                                   int64_t p, int64_t ld_in, float* __restrict__ Xf, double* __restrict__ Xd, int ld,
+                                   int* bad) {
+    const size_t total = (size_t)n * ld;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int64_t i = (int64_t)(k / ld), c = (int64_t)(k % ld);
+        float v = 0.f;
+        if (c < p) {
+            const bool obs = mask ? (mask[i * ld_in + c] != 0) : true;
+            if (obs) {
+                v = X[i * ld_in + c];
+                if (!isfinite(v)) {
+                    atomicAdd(bad, 1);
+                    v = 0.f;
+                }
+            }
+        }
+        Xf[k] = v;
+        if (Xd) Xd[k] = (double)v;
+    }
+}
+
+__global__ void pack_mask_kernel(const uint8_t* __restrict__ mask, int64_t n, int64_t p, int64_t ld_in,
+                                 uint32_t* __restrict__ bits, int ldw, int* empty_rows) {
+    // one block per row: build the words and count observed entries
+    const int64_t i = blockIdx.x;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int local = 0;
+    for (int wd = threadIdx.x; wd < ldw; wd += blockDim.x) {
+        uint32_t word = 0u;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t c = (int64_t)wd * 32 + b;
+            bool obs = true;
+            if (c < p) {
+                obs = mask[i * ld_in + c] != 0;
+                local += obs ? 1 : 0;
+            }
+            if (obs) word |= (1u << b);
+        }
+        bits[(size_t)i * ldw + wd] = word;
+    }
+    atomicAdd(&cnt, local);   // integer count: order does not matter
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt == 0) atomicAdd(empty_rows, 1);
+}
+
+__global__ void column_mean_kernel(const float* __restrict__ Xf, const uint32_t* __restrict__ bits, int n, int p,
+                                   int ld, int ldw, double* __restrict__ colmean) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p) return;
+    double s = 0.0;
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        const bool obs = bits ? ((bits[(size_t)i * ldw + (c >> 5)] >> (c & 31)) & 1u) : true;
+        if (obs) {
+            s += (double)Xf[(size_t)i * ld + c];
+            ++cnt;
+        }
+    }
+    colmean[c] = cnt > 0 ? s / cnt : 0.0;
+}
+
+__global__ void fill_kernel(const float* __restrict__ Xf, const uint32_t* __restrict__ bits, int n, int p, int ld,
+                            int ldw, const double* __restrict__ colmean, float* __restrict__ Y0f,
+                            double* __restrict__ Y0d) {
+    const size_t total = (size_t)n * ld;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k / ld), c = (int)(k % ld);
+        double y = 0.0;
+        if (c < p) {
+            const bool obs = bits ? ((bits[(size_t)i * ldw + (c >> 5)] >> (c & 31)) & 1u) : true;
+            y = obs ? (double)Xf[k] : colmean[c];
+        }
+        if (Y0f) Y0f[k] = (float)y;
+        if (Y0d) Y0d[k] = y;
+    }
+}
+
+// per-column sum of squared deviations of Y_0 (double), then one fixed-order total
+__global__ void centred_ss_kernel(const float* __restrict__ Y0f, const double* __restrict__ Y0d, int n, int p, int ld,
+                                  const double* __restrict__ colmean, double* __restrict__ colss) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p) return;
+    // mean of Y_0 over all rows equals the observed mean (missing rows hold it)
+    const double mu = colmean[c];
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double y = Y0d ? Y0d[(size_t)i * ld + c] : (double)Y0f[(size_t)i * ld + c];
+        s += (y - mu) * (y - mu);
+    }
+    colss[c] = s;
+}
+
+__global__ void total_kernel(const double* __restrict__ v, int len, double* __restrict__ out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s += v[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) t += red[k];
+        *out = t;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_input(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld_in, float* Xf,
+                              double* Xd, uint32_t* maskbits, int ld, int ldw, int* bad_count, cudaStream_t s) {
+    // bad_count[0]: non-finite observed entries, bad_count[1]: rows with nothing observed
+    size_t total = (size_t)n * ld;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    count_launches(1);
+    pack_values_kernel<<<blocks, 256, 0, s>>>(X, mask, n, p, ld_in, Xf, Xd, ld, bad_count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !mask) return e;
+    count_launches(1);
+    pack_mask_kernel<<<(unsigned)n, 128, 0, s>>>(mask, n, p, ld_in, maskbits, ldw, bad_count + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_missing(const float* Xf, const double* Xd, const uint32_t* maskbits, int n, int p, int ld,
+                                int ldw, double* colmean, float* Y0f, double* Y0d, double* ss, cudaStream_t s) {
+    (void)Xd;
+    const int tb = 128;
+    count_launches(1);
+    column_mean_kernel<<<(p + tb - 1) / tb, tb, 0, s>>>(Xf, maskbits, n, p, ld, ldw, colmean);
+    size_t total = (size_t)n * ld;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    count_launches(1);
+    fill_kernel<<<blocks, 256, 0, s>>>(Xf, maskbits, n, p, ld, ldw, colmean, Y0f, Y0d);
+    // the caller's colmean buffer holds 2 * ld doubles; the second half takes
+    // the per-column sums of squared deviations
+    double* colss = colmean + ld;
+    count_launches(1);
+    centred_ss_kernel<<<(p + tb - 1) / tb, tb, 0, s>>>(Y0f, Y0d, n, p, ld, colmean, colss);
+    count_launches(1);
+    total_kernel<<<1, 1024, 0, s>>>(colss, p, ss);
+    return cudaGetLastError();
+}
+
+}  // namespace ccx

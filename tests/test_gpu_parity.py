@@ -1,0 +1,232 @@
+"""Parity of the CUDA solver with the FP64 oracle, through the C ABI.
+
+Bar (stated per assertion):
+  * U: relative Frobenius error <= 1e-4 at every gamma (FP32 path), <= 1e-6
+    for the FP64 path (its output is rounded to float32 once);
+  * fused edge sets equal, except edges whose oracle margin
+    |mu w d / (rho ||b||) - 1| is below 1e-5 (both sides decide the same
+    comparison, in different rounding);
+  * labels identical whenever the fused sets are identical;
+  * kNN edge sets bit-exact, weights to 1e-12 relative.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MARGIN = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ccx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1409_2065_gb300 as m
+    return m
+
+
+def oracle_margins(r, X, mask, G):
+    A, B = O.project(r.U, r.V, G)
+    nb = np.linalg.norm(B, axis=1)
+    ratio = r.mu * G.w * r.d / (r.rho * np.maximum(nb, 1e-300))
+    return np.abs(ratio - 1.0)
+
+
+def compare_path(U, labels, stats, ref, X, mask, G, utol, tag=""):
+    for g, r in enumerate(ref):
+        err = np.linalg.norm(U[g].astype(np.float64) - r.U) / max(np.linalg.norm(r.U), 1e-300)
+        assert err <= utol, f"{tag} gamma={r.mu}: U rel err {err:.3e} > {utol}"
+        assert stats[g]["converged"] in (1, 2), f"{tag} gamma={r.mu} not converged"
+        near = oracle_margins(r, X, mask, G) < MARGIN
+        if not near.any():
+            assert stats[g]["n_fused"] == int(r.fused.sum()), f"{tag} gamma={r.mu} fused count"
+            assert np.array_equal(labels[g], r.labels), f"{tag} gamma={r.mu} labels differ"
+
+
+def knn_graph(X, mask, k, phi, normalize=False):
+    ei, ej, w, _, _ = O.knn_gaussian_weights(X.astype(np.float64), mask, k, phi, normalize)
+    return O.EdgeGraph(X.shape[0], ei, ej, w)
+
+
+@pytest.mark.parametrize("precision,utol", [(1, 1e-6), (0, 1e-4)])
+def test_tiny_path(ccx, precision, utol):
+    X, _ = synth.gaussian_mixture(12, 3, 3, seed=5)
+    G = knn_graph(X, None, 3, 0.1)
+    gammas = [0.0, 0.05, 0.5, 5.0, 50.0]
+    pr = ccx.Problem(X, None, precision)
+    pr.set_edges(G.ei, G.ej, G.w)
+    U, labels, stats, st = pr.solve_path(gammas)
+    ref = O.solve_path(X.astype(np.float64), None, G, gammas, tol=1e-12)
+    compare_path(U, labels, stats, ref, X, None, G, utol, "tiny")
+    assert np.linalg.norm(U[0] - X) <= 1e-5 * np.linalg.norm(X)   # gamma = 0 returns the data
+
+
+def test_ragged_missing_fp32(ccx):
+    """n = 70, p = 37 (ten 4-column slices, ragged last slice), 10 % missing."""
+    X, _ = synth.gaussian_mixture(70, 37, 4, seed=11)
+    rng = np.random.default_rng(12)
+    mask = synth.random_mask(rng, 70, 37, 0.1)
+    G = knn_graph(X, mask, 5, 0.02)
+    Y0 = O.fill_missing(X, mask)
+    g0 = O.fusion_scale(X, mask, G.ei, G.ej, G.w)
+    gammas = synth.log_grid(1e-2 * g0, 3.0 * g0, 5)
+    pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+    pr.set_edges(G.ei, G.ej, G.w)
+    assert abs(pr.fusion_scale() - g0) <= 1e-6 * g0
+    U, labels, stats, st = pr.solve_path(gammas)
+    ref = O.solve_path(X.astype(np.float64), mask, G, gammas, tol=1e-12)
+    compare_path(U, labels, stats, ref, X, mask, G, 1e-4, "ragged")
+    assert Y0.shape == X.shape
+
+
+@pytest.mark.parametrize("precision,utol", [(1, 1e-6), (0, 1e-4)])
+def test_plain_workload_against_stored_oracle(ccx, precision, utol):
+    """n = 200, p = 10, kNN k = 10, 20 gamma (values written by tests/golden/make_golden.py)."""
+    z = np.load(os.path.join(GOLDEN, "plain_n200_p10.npz"))
+    X = z["X"]
+    pr = ccx.Problem(X, None, precision)
+    pr.build_knn(10, phi=0.5)
+    ei, ej, w = pr.get_edges()
+    assert np.array_equal(ei, z["ei"]) and np.array_equal(ej, z["ej"])
+    assert np.allclose(w, z["w"], rtol=1e-12, atol=0)
+    U, labels, stats, st = pr.solve_path(z["gammas"])
+    G = O.EdgeGraph(200, z["ei"], z["ej"], z["w"])
+    for g in range(len(z["gammas"])):
+        err = np.linalg.norm(U[g] - z["U"][g]) / np.linalg.norm(z["U"][g])
+        assert err <= utol, (g, err)
+        assert stats[g]["converged"] in (1, 2)
+        if stats[g]["n_fused"] == int(z["fused"][g].sum()):
+            assert np.array_equal(labels[g], z["labels"][g]), g
+
+
+def test_knn_matches_oracle_missing_normalized(ccx):
+    X, _ = synth.gaussian_mixture(90, 23, 3, seed=21)
+    rng = np.random.default_rng(22)
+    mask = synth.random_mask(rng, 90, 23, 0.05)
+    pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+    pr.build_knn(7, phi_auto=True, normalize=True)
+    ei, ej, w = pr.get_edges()
+    oei, oej, ow, _, _ = O.knn_gaussian_weights(X.astype(np.float64), mask, 7, "auto", True)
+    assert np.array_equal(ei, oei) and np.array_equal(ej, oej)
+    assert np.allclose(w, ow, rtol=1e-12, atol=0)
+    assert abs(w.sum() - 1.0) < 1e-12
+
+
+def test_knn_all_pairs(ccx):
+    X, _ = synth.expression_like(20, 300, 3, 40, seed=2)
+    pr = ccx.Problem(X, None, ccx.CCX_FP32)
+    pr.build_knn(19, phi_auto=True, normalize=True)
+    ei, ej, w = pr.get_edges()
+    assert ei.size == 190
+    oei, oej, ow, _, _ = O.knn_gaussian_weights(X.astype(np.float64), None, 19, "auto", True)
+    assert np.array_equal(ei, oei) and np.allclose(w, ow, rtol=1e-12, atol=0)
+
+
+def test_edge_cases(ccx):
+    # a single case: no edges, U = X
+    X1 = np.array([[1.0, -2.0, 3.0]], np.float32)
+    pr = ccx.Problem(X1)
+    U, labels, stats, _ = pr.solve_path([0.0, 1.0])
+    assert np.allclose(U[:, 0], X1, atol=1e-6) and labels.tolist() == [[0], [0]]
+    # no edges at all: every case its own cluster, U = X
+    X, _ = synth.gaussian_mixture(9, 2, 3, seed=3)
+    pr = ccx.Problem(X)
+    U, labels, stats, _ = pr.solve_path([3.0])
+    assert np.allclose(U[0], X, atol=1e-5) and labels[0].tolist() == list(range(9))
+    # p = 1, a chain graph and a disconnected pair of components
+    Xc = np.array([[0.0], [0.1], [0.3], [10.0], [10.2]], np.float32)
+    pr = ccx.Problem(Xc, None, ccx.CCX_FP64)
+    pr.set_edges([0, 1, 3], [1, 2, 4], [1.0, 1.0, 1.0])
+    U, labels, stats, _ = pr.solve_path([100.0])
+    assert labels[0].tolist() == [0, 0, 0, 1, 1]
+    G = O.EdgeGraph(5, [0, 1, 3], [1, 2, 4], [1.0, 1.0, 1.0])
+    ref = O.solve_path(Xc.astype(np.float64), None, G, [100.0], tol=1e-12)
+    assert np.linalg.norm(U[0] - ref[0].U) <= 1e-6 * np.linalg.norm(ref[0].U)
+
+
+def test_complete_graph(ccx):
+    X, _ = synth.expression_like(16, 40, 3, 8, seed=4)
+    n = 16
+    ei, ej = np.triu_indices(n, 1)
+    w = np.full(ei.size, 1.0 / ei.size)
+    G = O.EdgeGraph(n, ei, ej, w)
+    g0 = O.fusion_scale(X, None, ei, ej, w)
+    gammas = [0.05 * g0, 0.3 * g0, 2.0 * g0]
+    pr = ccx.Problem(X)
+    pr.set_edges(ei, ej, w)
+    U, labels, stats, _ = pr.solve_path(gammas)
+    ref = O.solve_path(X.astype(np.float64), None, G, gammas, tol=1e-12)
+    compare_path(U, labels, stats, ref, X, None, G, 1e-4, "complete")
+
+
+def test_deterministic_and_device_outputs(ccx):
+    import torch
+    X, _ = synth.gaussian_mixture(50, 17, 3, seed=8)
+    G = knn_graph(X, None, 4, 0.05)
+    gammas = [0.1, 1.0]
+    outs = []
+    for _ in range(2):
+        pr = ccx.Problem(X)
+        pr.set_edges(G.ei, G.ej, G.w)
+        outs.append(pr.solve_path(gammas))
+        pr.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    pr = ccx.Problem(torch.from_numpy(X).cuda())
+    pr.set_edges(G.ei, G.ej, G.w)
+    Ud, Ld, _, _ = pr.solve_path(gammas, device=True)
+    assert np.array_equal(Ud.cpu().numpy(), outs[0][0]) and np.array_equal(Ld.cpu().numpy(), outs[0][1])
+
+
+def test_path_continues_across_calls(ccx):
+    X, _ = synth.gaussian_mixture(30, 5, 3, seed=9)
+    G = knn_graph(X, None, 4, 0.1)
+    gammas = [0.02, 0.2, 2.0]
+    pr = ccx.Problem(X)
+    pr.set_edges(G.ei, G.ej, G.w)
+    Ua, _, _, _ = pr.solve_path(gammas)
+    pr.reset_path()
+    Ub0, _, _, _ = pr.solve_path(gammas[:2])
+    Ub1, _, _, _ = pr.solve_path(gammas[2:])
+    ref = O.solve_path(X.astype(np.float64), None, G, gammas, tol=1e-12)
+    for g in range(3):
+        Ug = Ub0[g] if g < 2 else Ub1[g - 2]
+        for Uc in (Ua[g], Ug):
+            assert np.linalg.norm(Uc - ref[g].U) <= 1e-4 * np.linalg.norm(ref[g].U)
+
+
+def test_invalid_inputs(ccx):
+    X, _ = synth.gaussian_mixture(6, 2, 2, seed=1)
+    bad = X.copy()
+    bad[2, 1] = np.nan
+    with pytest.raises(ccx.CcxError) as e:
+        ccx.Problem(bad)
+    assert e.value.status == 1
+    m = np.ones((6, 2), np.uint8)
+    m[3, :] = 0
+    with pytest.raises(ccx.CcxError) as e:
+        ccx.Problem(X, m)
+    assert e.value.status == 1
+    bad_m = bad.copy()
+    mm = np.ones((6, 2), np.uint8)
+    mm[2, 1] = 0      # the NaN is masked out: accepted
+    ccx.Problem(bad_m, mm).close()
+    pr = ccx.Problem(X)
+    for ei, ej, w in (([0], [0], [1.0]), ([1], [0], [1.0]), ([0], [9], [1.0]), ([0], [1], [-1.0]),
+                      ([0, 0], [1, 1], [1.0, 1.0]), ([0], [1], [np.inf])):
+        with pytest.raises(ccx.CcxError) as e:
+            pr.set_edges(ei, ej, w)
+        assert e.value.status == 1
+    pr.set_edges([0, 1], [1, 2], [1.0, 0.0])     # zero weight dropped
+    assert pr.get_edges()[0].size == 1
+    with pytest.raises(ccx.CcxError) as e:
+        pr.solve_path([-1.0])
+    assert e.value.status == 1
+    with pytest.raises(ccx.CcxError) as e:
+        pr.solve_path([np.nan])
+    assert e.value.status == 1
