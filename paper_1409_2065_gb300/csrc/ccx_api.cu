@@ -17,7 +17,6 @@
 
 namespace ccx {
 void knn_set_exact_rows(const float* Xf, const uint32_t* bits, const double* colmean, int ldw);
-int reduce_blocks(int m);
 }  // namespace ccx
 
 using namespace ccx;
@@ -100,8 +99,12 @@ struct ccx_problem {
     int* d_ej = nullptr;
     double* d_w = nullptr;
     int* d_rowptr = nullptr;
-    int* d_col = nullptr;
-    int* d_eid = nullptr;
+    int* d_nc0 = nullptr;
+    uint16_t* d_csr = nullptr;
+    int* d_qpos = nullptr;
+    uint2* d_nchunk = nullptr;
+    uint4* d_echunk = nullptr;
+    int nch = 0, ech = 0;
     // path state
     void* A[2] = {nullptr, nullptr};
     float* Alo[2] = {nullptr, nullptr};
@@ -109,7 +112,7 @@ struct ccx_problem {
     void* Q = nullptr;
     void* Em = nullptr;
     void* t[2] = {nullptr, nullptr};
-    double* Pnb = nullptr;
+    float* Pnb = nullptr;
     double* Ps = nullptr;
     double* nb = nullptr;
     uint8_t* fused = nullptr;
@@ -154,7 +157,8 @@ void free_path(ccx_problem* pr) {
     if (pr->h_ncl) cudaFreeHost(pr->h_ncl);
     if (pr->graph) cudaGraphExecDestroy(pr->graph);
     pr->Q = pr->Em = nullptr;
-    pr->Pnb = pr->Ps = pr->nb = nullptr;
+    pr->Pnb = nullptr;
+    pr->Ps = pr->nb = nullptr;
     pr->fused = nullptr;
     pr->Rf = nullptr;
     pr->st = nullptr;
@@ -172,9 +176,16 @@ void free_edges(ccx_problem* pr) {
     cudaFree(pr->d_ej);
     cudaFree(pr->d_w);
     cudaFree(pr->d_rowptr);
-    cudaFree(pr->d_col);
-    cudaFree(pr->d_eid);
-    pr->d_ei = pr->d_ej = pr->d_rowptr = pr->d_col = pr->d_eid = nullptr;
+    cudaFree(pr->d_nc0);
+    cudaFree(pr->d_csr);
+    cudaFree(pr->d_qpos);
+    pr->d_qpos = nullptr;
+    cudaFree(pr->d_nchunk);
+    cudaFree(pr->d_echunk);
+    pr->d_ei = pr->d_ej = pr->d_rowptr = pr->d_nc0 = nullptr;
+    pr->d_csr = nullptr;
+    pr->d_nchunk = nullptr;
+    pr->d_echunk = nullptr;
     pr->d_w = nullptr;
 }
 
@@ -260,30 +271,65 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
         ent[fillp[pr->ei[q]]++] = {pr->ej[q], q};
         ent[fillp[pr->ej[q]]++] = {pr->ei[q], q};
     }
-    std::vector<int> col(2 * (size_t)m), eid(2 * (size_t)m);
+    // entries: neighbour index; rowmid[i] = first entry with neighbour > i; qpos: the two
+    // CSR positions of each edge (its entry in the smaller endpoint's row, then the larger's)
+    std::vector<uint16_t> csr(2 * (size_t)m);
+    std::vector<int> rowmid(n, 0), qpos(2 * (size_t)m, 0);
     for (int64_t i = 0; i < n; ++i) {
         std::sort(ent.begin() + rowptr[i], ent.begin() + rowptr[i + 1]);
+        rowmid[i] = rowptr[i + 1];
+        for (int k = rowptr[i + 1] - 1; k >= rowptr[i]; --k)
+            if (ent[k].first > i) rowmid[i] = k;
         for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-            col[k] = ent[k].first;
-            eid[k] = ent[k].second;
+            csr[k] = (uint16_t)ent[k].first;
+            const int e = ent[k].second;
+            qpos[2 * (size_t)e + (ent[k].first > i ? 0 : 1)] = k;
         }
     }
+    // work items of the iteration kernel: runs of <= kChunk CSR entries of one node
+    // (all neighbours for the node phase; the larger-index ones for the edge phase)
+    std::vector<uint2> nchunk;
+    std::vector<uint4> echunk;
+    std::vector<int> nc0(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        nc0[i] = (int)nchunk.size();
+        for (int q = rowptr[i]; q < rowptr[i + 1]; q += kChunk)
+            nchunk.push_back(make_uint2((uint32_t)q, (uint32_t)i | ((uint32_t)std::min(kChunk, rowptr[i + 1] - q) << 16)));
+        for (int q = rowmid[i]; q < rowptr[i + 1]; q += kChunk) {
+            // edges are sorted by (i, j): the entries of row i with j > i are edges
+            // ebase, ebase + 1, ... in order
+            const int e = ent[q].second;
+            echunk.push_back(make_uint4((uint32_t)q, (uint32_t)i | ((uint32_t)std::min(kChunk, rowptr[i + 1] - q) << 16),
+                                        (uint32_t)e, 0u));
+        }
+    }
+    nc0[n] = (int)nchunk.size();
     free_path(pr);
     free_edges(pr);
     CUDA_TRY(dalloc(&pr->d_ei, m));
     CUDA_TRY(dalloc(&pr->d_ej, m));
     CUDA_TRY(dalloc(&pr->d_w, m));
     CUDA_TRY(dalloc(&pr->d_rowptr, n + 1));
-    CUDA_TRY(dalloc(&pr->d_col, 2 * (size_t)m));
-    CUDA_TRY(dalloc(&pr->d_eid, 2 * (size_t)m));
+    CUDA_TRY(dalloc(&pr->d_nc0, n + 1));
+    CUDA_TRY(dalloc(&pr->d_csr, 2 * (size_t)m));
+    CUDA_TRY(dalloc(&pr->d_qpos, 2 * (size_t)m));
+    CUDA_TRY(dalloc(&pr->d_nchunk, nchunk.size()));
+    CUDA_TRY(dalloc(&pr->d_echunk, echunk.size()));
+    pr->nch = (int)nchunk.size();
+    pr->ech = (int)echunk.size();
+    if (!nchunk.empty())
+        CUDA_TRY(cudaMemcpy(pr->d_nchunk, nchunk.data(), sizeof(uint2) * nchunk.size(), cudaMemcpyHostToDevice));
+    if (!echunk.empty())
+        CUDA_TRY(cudaMemcpy(pr->d_echunk, echunk.data(), sizeof(uint4) * echunk.size(), cudaMemcpyHostToDevice));
     if (m > 0) {
         CUDA_TRY(cudaMemcpy(pr->d_ei, pr->ei.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(pr->d_ej, pr->ej.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(pr->d_w, pr->w.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(pr->d_col, col.data(), sizeof(int) * 2 * m, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(pr->d_eid, eid.data(), sizeof(int) * 2 * m, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(pr->d_csr, csr.data(), sizeof(uint16_t) * 2 * m, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(pr->d_qpos, qpos.data(), sizeof(int) * 2 * m, cudaMemcpyHostToDevice));
     }
     CUDA_TRY(cudaMemcpy(pr->d_rowptr, rowptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_nc0, nc0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     return CCX_OK;
 }
 
@@ -301,8 +347,13 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.Q = reinterpret_cast<R*>(pr->Q);
     P.Em = reinterpret_cast<R*>(pr->Em);
     P.rowptr = pr->d_rowptr;
-    P.col = pr->d_col;
-    P.eid = pr->d_eid;
+    P.csr = pr->d_csr;
+    P.qpos = pr->d_qpos;
+    P.nchunk = pr->d_nchunk;
+    P.echunk = pr->d_echunk;
+    P.nc0 = pr->d_nc0;
+    P.nch = pr->nch;
+    P.ech = pr->ech;
     P.ei = pr->d_ei;
     P.ej = pr->d_ej;
     P.w = pr->d_w;
@@ -323,15 +374,17 @@ IterParams<R> make_params(ccx_problem* pr) {
 
 ccx_status check_limits(ccx_problem* pr) {
     const int m = (int)pr->ei.size();
+    if (pr->n > 65535 || m > 65535)
+        return fail(CCX_EUNSUPPORTED, "the iteration kernel packs node and edge indices in 16 bits: n and the "
+                                      "number of edges must be <= 65535 (have %lld, %d)", (long long)pr->n, m);
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pr->device));
-    const size_t need = pd_slice_smem_bytes((int)pr->n, m, pr->precision == CCX_FP64);
+    const size_t need = pd_slice_smem_bytes((int)pr->n, m, pr->nch, pr->ech, pr->precision == CCX_FP64, false);
     if (need + 2048 > (size_t)optin)
         return fail(CCX_EUNSUPPORTED,
                     "n = %lld cases and %d edges need %zu bytes of shared memory per block (a column slice of "
-                    "all rows, %d bytes per row, plus 8 bytes per edge); the device allows %d",
-                    (long long)pr->n, m, need, pr->precision == CCX_FP64 ? 4 * kSliceCols * 8 : 6 * kSliceCols * 4,
-                    optin);
+                    "all rows plus 12 bytes per edge); the device allows %d",
+                    (long long)pr->n, m, need, optin);
     return CCX_OK;
 }
 
@@ -347,7 +400,7 @@ ccx_status ensure_path(ccx_problem* pr) {
         CUDA_TRY(cudaMalloc(&pr->A[k], es * nl));
         CUDA_TRY(cudaMalloc(&pr->Dl[k], es * nl));
         if (!fp64) CUDA_TRY(dalloc(&pr->Alo[k], nl));
-        CUDA_TRY(cudaMalloc(&pr->t[k], es * std::max(m, 1)));
+        CUDA_TRY(cudaMalloc(&pr->t[k], es * 4 * std::max(m, 1)));   // a (t, t_prev) pair per CSR entry
     }
     if (pr->has_mask) {
         CUDA_TRY(cudaMalloc(&pr->Q, es * nl));
@@ -357,7 +410,7 @@ ccx_status ensure_path(ccx_problem* pr) {
     CUDA_TRY(dalloc(&pr->Ps, (size_t)pr->G * kNumScalarPartials));
     CUDA_TRY(dalloc(&pr->nb, m));
     CUDA_TRY(dalloc(&pr->fused, m));
-    CUDA_TRY(dalloc(&pr->Rf, 2 * 128));
+    CUDA_TRY(dalloc(&pr->Rf, 2 * (size_t)pd_reduce_blocks(m)));
     CUDA_TRY(dalloc(&pr->st, 1));
     CUDA_TRY(cudaMallocHost(&pr->st_host, 2 * sizeof(PdState)));
     CUDA_TRY(dalloc(&pr->Ustage, (size_t)pr->n * pr->p));

@@ -23,13 +23,14 @@ namespace ccx {
 
 constexpr int kSliceThreads = 512;   // threads of the fused iteration kernel
 constexpr int kSliceCols = 4;        // columns per staged slice (one 16-byte vector for float)
+constexpr int kChunk = 16;           // neighbours per work item of the iteration kernel
 constexpr int kReduceThreads = 256;
 constexpr int kConvWindow = 64;      // iterations per convergence window
 constexpr int kRateWindows = 8;      // windows spanned by the contraction-rate estimate
 constexpr int kNumScalarPartials = 8;
 constexpr double kStallSteps = 128.0;  // error bound, in steps, once steps are at the rounding level
-constexpr double kNoiseFactor = 32.0;  // steps within this factor of the rounding noise: no progress possible
-constexpr int kNoiseWindows = 4;       // consecutive such windows before stopping
+constexpr double kNoiseFactor = 8.0;   // steps within this factor of the rounding noise: no progress possible
+constexpr int kNoiseWindows = 8;       // consecutive such windows before stopping
 
 // Scalar partial slots written by each CTA of the iteration kernel.
 enum : int {
@@ -82,20 +83,24 @@ struct IterParams {
     R* Dl[2];                   // velocity slots Delta = A_m - A_{m-1}
     R* Q;                       // missing entries: U_y - A of the last iteration
     R* Em;                      // missing entries: U - A_prev of the last iteration
-    R* t[2];                    // per-edge t = 1 - s slots
+    R* t[2];                    // per CSR entry, interleaved (t_m, t_{m-1}) of its edge, t = 1 - s
     const int* rowptr;          // CSR over both directions, n + 1
-    const int* col;             // neighbour of each CSR entry
-    const int* eid;             // edge id of each CSR entry
+    const uint16_t* csr;        // CSR entries: neighbour index
+    const int* qpos;            // per edge: its two CSR positions (from the smaller, then the larger endpoint)
+    const uint2* nchunk;        // node-phase work items: (first CSR entry, node | length << 16)
+    const uint4* echunk;        // edge-phase work items over the entries with a larger neighbour:
+                                // (first CSR entry, node | length << 16, first edge id, 0)
+    const int* nc0;             // n + 1: first node-phase work item of each node
     const int* ei;              // edge endpoints, i < j
     const int* ej;
     const double* w;            // edge weights
-    double* Pnb;                // per-CTA per-edge partial ||b||^2, G x m
+    float* Pnb;                 // per-CTA per-edge partial ||b||^2, G x m
     double* Ps;                 // per-CTA scalar partials, G x kNumScalarPartials
     double* nb;                 // per-edge ||b_m|| of the last iteration
     uint8_t* fused;             // per-edge fused flag of t_{m+1}
     unsigned long long* Rf;     // per reduce-block fused count / hash
     PdState* st;
-    int n, ld, ldw, m, nslices, G;
+    int n, ld, ldw, m, nslices, G, nch, ech;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -115,7 +120,8 @@ cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s);
 void count_launches(unsigned long long k);
 template <typename R>
 cudaError_t launch_pd_finalize(const IterParams<R>& P, float* U_out, int64_t ld_out, int p, cudaStream_t s);
-size_t pd_slice_smem_bytes(int n, int m, bool fp64);
+size_t pd_slice_smem_bytes(int n, int m, int nch, int ech, bool fp64, bool prefetch);
+int pd_reduce_blocks(int m);
 
 // data preparation (prep_kernels.cu)
 cudaError_t launch_pack_input(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld_in,

@@ -95,7 +95,55 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
 }
 
 // ------------------------------------------------------------------ slice
+// 16-byte asynchronous global->shared copy (cp.async.cg bypasses L1).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void copy_vec_async(T* dst, const T* src) {
+    static_assert(sizeof(T) % 16 == 0, "vector rows are multiples of 16 bytes");
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(T) / 16); ++k)
+        cp_async16(reinterpret_cast<char*>(dst) + 16 * k, reinterpret_cast<const char*>(src) + 16 * k);
+}
+
+// Shared-memory layout of the iteration kernel (all offsets multiples of 16 bytes):
+//   per staging buffer b in {0, 1 (prefetch only)}:
+//       A_hi[n], (A_lo[n] on the FP32 path), Delta_{m-1}[n], X[n], mask word[n]
+//   Delta_m[n]
+//   Gpart[nchunks]               (partial correction sums of the node-phase work items)
+//   echunk[echunks]              (edge work items: first entry, node | length << 16, first edge, 0)
+//   nchunk[nchunks]              (node work items: first entry, node | length << 16)
+//   rowptr[n + 1], nc0[n + 1]    (nc0[i]: first node-phase work item of node i)
+//   nbacc[m]                     (float: this CTA's sum of ||b_m||^2 over its slices)
+//   csr[2 m]                     (uint16 neighbour index)
 template <typename R>
+struct SliceLayout {
+    static constexpr bool FF = std::is_same<R, float>::value;
+    static constexpr size_t row = sizeof(R) * C;             // bytes of one row slice
+    // A_hi (+A_lo) + Delta_{m-1} + X + mask word (padded to 16 bytes)
+    static constexpr size_t buf = (FF ? 4 : 3) * row + 16;
+    static size_t bytes(int n, int m, int nch, int ech, bool pref) {
+        size_t b = (pref ? 2 : 1) * buf * (size_t)n + row * (size_t)n;
+        b += row * (size_t)nch;
+        b += sizeof(uint4) * (size_t)ech + sizeof(uint2) * (size_t)nch;
+        b += sizeof(int) * 2 * (size_t)(n + 1);
+        b = (b + 15) / 16 * 16;
+        b += sizeof(float) * (size_t)m;
+        b += sizeof(uint16_t) * 2 * (size_t)m;
+        return (b + 15) / 16 * 16;
+    }
+};
+
+template <typename R, bool PREF>
 __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R> P) {
     constexpr bool FF = std::is_same<R, float>::value;
     using V = Vec<R, C>;
@@ -103,7 +151,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     const PdState* st = P.st;
     if (st->done) return;
 
-    const int n = P.n, ld = P.ld, m = P.m, tid = threadIdx.x;
+    const int n = P.n, ld = P.ld, m = P.m, tid = threadIdx.x, G = gridDim.x;
+    const int nch = P.nch, ech = P.ech;
     const int par = st->par;
     const R beta = (R)st->beta;
     const R onepb = (R)(1.0 + st->beta);
@@ -115,50 +164,120 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     float* __restrict__ Alo_out = P.Alo[par ^ 1];
     const R* __restrict__ D1g = P.Dl[par];       // Delta_{m-1}
     R* __restrict__ D0g = P.Dl[par ^ 1];         // Delta_m (written)
-    const R* __restrict__ tm = P.t[par];         // t_m
-    const R* __restrict__ tm1 = P.t[par ^ 1];    // t_{m-1}
+    const Vec<R, 2>* __restrict__ tq = reinterpret_cast<const Vec<R, 2>*>(P.t[par]);  // (t_m, t_{m-1}) per entry
     const R* __restrict__ Xg = P.X;
     const uint32_t* __restrict__ maskg = P.mask;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* sAhi = reinterpret_cast<V*>(smem_raw);
-    V* sD1 = sAhi + n;
-    V* sOhi = sD1 + n;
-    V* sD0 = sOhi + n;
-    VF* sAlo = reinterpret_cast<VF*>(sD0 + n);
-    VF* sOlo = sAlo + (FF ? n : 0);
-    double* sNb = reinterpret_cast<double*>(sOlo + (FF ? n : 0));   // per-edge ||b||^2 over this CTA's slices
+    unsigned char* sp = smem_raw;
+    V* bAhi[2];
+    VF* bAlo[2];
+    V* bD1[2];
+    V* bX[2];
+    uint32_t* bM[2];
+    for (int b = 0; b < (PREF ? 2 : 1); ++b) {
+        bAhi[b] = reinterpret_cast<V*>(sp);
+        sp += sizeof(V) * (size_t)n;
+        bAlo[b] = reinterpret_cast<VF*>(sp);
+        if (FF) sp += sizeof(VF) * (size_t)n;
+        bD1[b] = reinterpret_cast<V*>(sp);
+        sp += sizeof(V) * (size_t)n;
+        bX[b] = reinterpret_cast<V*>(sp);
+        sp += sizeof(V) * (size_t)n;
+        bM[b] = reinterpret_cast<uint32_t*>(sp);
+        sp += 16 * (size_t)n;
+    }
+    if (!PREF) {
+        bAhi[1] = bAhi[0];
+        bAlo[1] = bAlo[0];
+        bD1[1] = bD1[0];
+        bX[1] = bX[0];
+        bM[1] = bM[0];
+    }
+    V* sD0 = reinterpret_cast<V*>(sp);
+    sp += sizeof(V) * (size_t)n;
+    V* sPart = reinterpret_cast<V*>(sp);
+    sp += sizeof(V) * (size_t)nch;
+    uint4* sEch = reinterpret_cast<uint4*>(sp);
+    sp += sizeof(uint4) * (size_t)ech;
+    uint2* sNch = reinterpret_cast<uint2*>(sp);
+    sp += sizeof(uint2) * (size_t)nch;
+    int* sRow = reinterpret_cast<int*>(sp);
+    int* sNc0 = sRow + n + 1;
+    sp += sizeof(int) * 2 * (size_t)(n + 1);
+    sp = smem_raw + ((size_t)(sp - smem_raw) + 15) / 16 * 16;
+    float* sNb = reinterpret_cast<float*>(sp);
+    sp += sizeof(float) * (size_t)m;
+    uint16_t* sCsr = reinterpret_cast<uint16_t*>(sp);
     __shared__ double red[32];
-    for (int e = tid; e < m; e += kSliceThreads) sNb[e] = 0.0;
+
+    auto stage = [&](int sl, int b) {
+        const int c0 = sl * C;
+        V* dA = b ? bAhi[1] : bAhi[0];
+        VF* dL = b ? bAlo[1] : bAlo[0];
+        V* dD = b ? bD1[1] : bD1[0];
+        V* dX = b ? bX[1] : bX[0];
+        uint32_t* dM = b ? bM[1] : bM[0];
+        for (int i = tid; i < n; i += kSliceThreads) {
+            const size_t off = (size_t)i * ld + c0;
+            copy_vec_async(&dA[i], reinterpret_cast<const V*>(Ahi_in + off));
+            copy_vec_async(&dD[i], reinterpret_cast<const V*>(D1g + off));
+            copy_vec_async(&dX[i], reinterpret_cast<const V*>(Xg + off));
+            if constexpr (FF) copy_vec_async(&dL[i], reinterpret_cast<const VF*>(Alo_in + off));
+            if (maskg) cp_async4(&dM[4 * i], maskg + (size_t)i * P.ldw + (c0 >> 5));
+        }
+        cp_async_commit();
+    };
+
+    int cur = 0;
+    if (blockIdx.x < P.nslices) stage(blockIdx.x, 0);
+    // launch-constant graph data
+    for (int k = tid; k <= n; k += kSliceThreads) {
+        sRow[k] = P.rowptr[k];
+        sNc0[k] = P.nc0[k];
+    }
+    for (int k = tid; k < 2 * m; k += kSliceThreads) sCsr[k] = P.csr[k];
+    for (int k = tid; k < nch; k += kSliceThreads) sNch[k] = P.nchunk[k];
+    for (int k = tid; k < ech; k += kSliceThreads) sEch[k] = P.echunk[k];
+    for (int e = tid; e < m; e += kSliceThreads) sNb[e] = 0.f;
     double s_ua = 0.0, s_vb = 0.0, s_rs = 0.0, s_st = 0.0, s_na = 0.0, s_nz = 0.0, s_dl = 0.0;
 
-    for (int sl = blockIdx.x; sl < P.nslices; sl += gridDim.x) {
+    for (int sl = blockIdx.x; sl < P.nslices; sl += G) {
         const int c0 = sl * C;
-        // ---- stage A_{m-1} and Delta_{m-1} of this slice for all rows
-        for (int i = tid; i < n; i += kSliceThreads) {
-            const size_t off = (size_t)i * ld + c0;
-            sAhi[i] = *reinterpret_cast<const V*>(Ahi_in + off);
-            sD1[i] = *reinterpret_cast<const V*>(D1g + off);
-            if constexpr (FF) sAlo[i] = *reinterpret_cast<const VF*>(Alo_in + off);
-        }
+        if (!PREF && sl != (int)blockIdx.x) stage(sl, 0);
+        cp_async_wait_all();
         __syncthreads();
+        if (PREF && sl + G < P.nslices) stage(sl + G, cur ^ 1);
+        const V* __restrict__ sAhi = cur ? bAhi[1] : bAhi[0];
+        const VF* __restrict__ sAlo = cur ? bAlo[1] : bAlo[0];
+        const V* __restrict__ sD1 = cur ? bD1[1] : bD1[0];
+        const V* __restrict__ sX = cur ? bX[1] : bX[0];
+        const uint32_t* __restrict__ sM = cur ? bM[1] : bM[0];
+        float f_ua = 0.f, f_vb = 0.f, f_rs = 0.f, f_st = 0.f, f_na = 0.f, f_nz = 0.f, f_dl = 0.f;
 
-        // ---- node phase: one Jacobi correction per node (i, slice)
-        for (int i = tid; i < n; i += kSliceThreads) {
-            const size_t off = (size_t)i * ld + c0;
+        // ---- node phase A: work items of <= kChunk neighbours (hubs of the kNN graph
+        //      have ~15x the median degree; splitting keeps the warps balanced)
+        for (int k = tid; k < nch; k += kSliceThreads) {
+            const uint2 ch = sNch[k];
+            const int i = (int)(ch.y & 0xFFFFu), len = (int)(ch.y >> 16);
+            const int r0 = (int)ch.x, r1 = r0 + len;
             const V a = sAhi[i];
             const V d1 = sD1[i];
             VF al;
             if constexpr (FF) al = sAlo[i];
-            R G[C];
+            R G_[C];
 #pragma unroll
-            for (int c = 0; c < C; ++c) G[c] = (R)0;
-            const int r0 = P.rowptr[i], r1 = P.rowptr[i + 1];
+            for (int c = 0; c < C; ++c) G_[c] = (R)0;
+            // (t_m, t_{m-1}) are stored per CSR entry: a sequential read, two kept in flight
+            Vec<R, 2> tq0 = tq[r0], tq1;
+            if (r0 + 1 < r1) tq1 = tq[r0 + 1];
             for (int q = r0; q < r1; ++q) {
-                const int j = __ldg(P.col + q);
-                const int e = __ldg(P.eid + q);
-                const R ca = onepb * __ldg(tm + e);
-                const R cb = beta * __ldg(tm1 + e);
+                const Vec<R, 2> t2 = tq0;
+                tq0 = tq1;
+                if (q + 2 < r1) tq1 = tq[q + 2];
+                const int j = sCsr[q];
+                const R ca = onepb * t2.v[0];
+                const R cb = beta * t2.v[1];
                 const V bj = sAhi[j];
                 const V dj = sD1[j];
                 VF lj;
@@ -168,15 +287,63 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
                     R b1 = a.v[c] - bj.v[c];
                     if constexpr (FF) b1 += al.v[c] - lj.v[c];
                     const R b2 = b1 - (d1.v[c] - dj.v[c]);
-                    G[c] += ca * b1 - cb * b2;
+                    G_[c] += ca * b1 - cb * b2;
                 }
             }
-            const R inv = (R)1 / (R)(1 + (r1 - r0));
-            const V x = *reinterpret_cast<const V*>(Xg + off);
-            uint32_t obs = 0xFu;
-            if (maskg) obs = (maskg[(size_t)i * P.ldw + (c0 >> 5)] >> (c0 & 31)) & 0xFu;
-            V ohi, dm;
-            VF olo;
+            V gp;
+#pragma unroll
+            for (int c = 0; c < C; ++c) gp.v[c] = G_[c];
+            sPart[k] = gp;
+        }
+        __syncthreads();
+
+        // ---- node phase B: one preconditioned correction of the projection per (i, slice)
+        // missing entries of this thread's first two nodes: issue their loads together
+        V qv0, qv1, ev0, ev1;
+        if (maskg) {
+            const int i0 = tid, i1 = tid + kSliceThreads;
+            if (i0 < n && ((sM[4 * i0] >> (c0 & 31)) & 0xFu) != 0xFu) {
+                qv0 = *reinterpret_cast<const V*>(P.Q + (size_t)i0 * ld + c0);
+                ev0 = *reinterpret_cast<const V*>(P.Em + (size_t)i0 * ld + c0);
+            }
+            if (i1 < n && ((sM[4 * i1] >> (c0 & 31)) & 0xFu) != 0xFu) {
+                qv1 = *reinterpret_cast<const V*>(P.Q + (size_t)i1 * ld + c0);
+                ev1 = *reinterpret_cast<const V*>(P.Em + (size_t)i1 * ld + c0);
+            }
+        }
+        for (int i = tid, u = 0; i < n; i += kSliceThreads, ++u) {
+            const size_t off = (size_t)i * ld + c0;
+            const V x = sX[i];
+            const uint32_t obs = maskg ? (sM[4 * i] >> (c0 & 31)) & 0xFu : 0xFu;
+            V qv, ev;
+            if (obs != 0xFu) {
+                if (u == 0) {
+                    qv = qv0;
+                    ev = ev0;
+                } else if (u == 1) {
+                    qv = qv1;
+                    ev = ev1;
+                } else {
+                    qv = *reinterpret_cast<const V*>(P.Q + off);
+                    ev = *reinterpret_cast<const V*>(P.Em + off);
+                }
+            }
+            const V a = sAhi[i];
+            const V d1 = sD1[i];
+            VF al;
+            if constexpr (FF) al = sAlo[i];
+            R G_[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) G_[c] = (R)0;
+            for (int k = sNc0[i]; k < sNc0[i + 1]; ++k) {     // fixed order: deterministic
+                const V gp = sPart[k];
+#pragma unroll
+                for (int c = 0; c < C; ++c) G_[c] += gp.v[c];
+            }
+            // preconditioner P = I + 2 Deg >= I + L: the sweep's iteration matrix
+            // has eigenvalues in [0, 1), which the extrapolation needs
+            const R inv = (R)1 / (R)(1 + 2 * (sRow[i + 1] - sRow[i]));
+            V dm;
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 R lo = (R)0;
@@ -187,76 +354,104 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
                     Em = alpha1 * xm;                          // U_m - A_{m-1}
                     Em1 = alpha2 * (xm + d1.v[c]);             // U_{m-1} - A_{m-2}
                 } else {
-                    Em = alpha1 * P.Q[off + c];
-                    Em1 = P.Em[off + c];
+                    Em = alpha1 * qv.v[c];
+                    Em1 = ev.v[c];
                 }
                 const R ue = onepb * Em - beta * Em1;          // U_y - A_start
-                const R delta = (ue - G[c]) * inv;             // A_m - A_start
+                const R delta = (ue - G_[c]) * inv;            // A_m - A_start
                 const R inc = beta * d1.v[c] + delta;          // A_m - A_{m-1}
-                if constexpr (FF) {
-                    float h, l;
-                    ff_add(a.v[c], al.v[c], inc, h, l);
-                    ohi.v[c] = h;
-                    olo.v[c] = l;
-                } else {
-                    ohi.v[c] = a.v[c] + inc;
-                }
                 dm.v[c] = inc;
                 if (!(obs & (1u << c))) {
                     P.Q[off + c] = ue - delta;                 // U_y - A_m
                     P.Em[off + c] = Em;
                 }
-                const double nz = ((double)fabs(ue) + (double)fabs(G[c])) * (double)inv;
-                s_nz += nz * nz;
-                s_dl += (double)delta * (double)delta;
-                const double r_ua = (double)(ue - delta);
-                s_ua += r_ua * r_ua;
-                s_rs += -(double)delta * (double)inc;
-                s_st += (double)inc * (double)inc;
-                s_na += (double)ohi.v[c] * (double)ohi.v[c];
+                const float nz = (float)((fabs(ue) + fabs(G_[c])) * inv);
+                f_nz += nz * nz;
+                f_dl += (float)(delta * delta);
+                const float r_ua = (float)(ue - delta);
+                f_ua += r_ua * r_ua;
+                f_rs -= (float)(delta * inc);
+                f_st += (float)(inc * inc);
             }
-            *reinterpret_cast<V*>(Ahi_out + off) = ohi;
-            *reinterpret_cast<V*>(D0g + off) = dm;
-            sOhi[i] = ohi;
-            sD0[i] = dm;
             if constexpr (FF) {
+                V ohi;
+                VF olo;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float h, l;
+                    ff_add(a.v[c], al.v[c], dm.v[c], h, l);
+                    ohi.v[c] = h;
+                    olo.v[c] = l;
+                    f_na += h * h;
+                }
+                *reinterpret_cast<V*>(Ahi_out + off) = ohi;
                 *reinterpret_cast<VF*>(Alo_out + off) = olo;
-                sOlo[i] = olo;
+            } else {
+                V ohi;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    ohi.v[c] = a.v[c] + dm.v[c];
+                    f_na += (float)(ohi.v[c] * ohi.v[c]);
+                }
+                *reinterpret_cast<V*>(Ahi_out + off) = ohi;
             }
+            *reinterpret_cast<V*>(D0g + off) = dm;
+            sD0[i] = dm;
         }
         __syncthreads();
 
-        // ---- edge phase: per-edge ||b_m||^2 and ||V_y - B_m||^2 on this slice
-        for (int e = tid; e < m; e += kSliceThreads) {
-            const int u = __ldg(P.ei + e), v = __ldg(P.ej + e);
-            const R ta = onepb * __ldg(tm + e);
-            const R tb = beta * __ldg(tm1 + e);
-            const V hu = sOhi[u], hv = sOhi[v];
-            const V mu_ = sD0[u], mv = sD0[v];
-            const V pu = sD1[u], pv = sD1[v];
-            VF lu, lv;
-            if constexpr (FF) {
-                lu = sOlo[u];
-                lv = sOlo[v];
-            }
-            R sb = (R)0, sv = (R)0;
+        // ---- edge phase, over work items of <= kChunk edges (i, j > i):
+        //      b_m = b_{m-1} + (Delta_m,i - Delta_m,j); ||b_m||^2 and ||V_y - B_m||^2
+        for (int k = tid; k < ech; k += kSliceThreads) {
+            const uint4 ch = sEch[k];
+            const int i = (int)(ch.y & 0xFFFFu), len = (int)(ch.y >> 16);
+            const int r0 = (int)ch.x, r1 = r0 + len, e0 = (int)ch.z - r0;
+            const V a = sAhi[i];
+            const V d1 = sD1[i];
+            const V d0 = sD0[i];
+            VF al;
+            if constexpr (FF) al = sAlo[i];
+            Vec<R, 2> tq0 = tq[r0], tq1;
+            if (r0 + 1 < r1) tq1 = tq[r0 + 1];
+            for (int q = r0; q < r1; ++q) {
+                const Vec<R, 2> t2 = tq0;
+                tq0 = tq1;
+                if (q + 2 < r1) tq1 = tq[q + 2];
+                const int j = sCsr[q], e = e0 + q;        // edges are numbered in (i, j) order
+                const R ta = onepb * t2.v[0];
+                const R tb = beta * t2.v[1];
+                const V bj = sAhi[j];
+                const V d1j = sD1[j];
+                const V d0j = sD0[j];
+                VF lj;
+                if constexpr (FF) lj = sAlo[j];
+                R sb = (R)0, sv = (R)0;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                R b = hu.v[c] - hv.v[c];
-                if constexpr (FF) b += lu.v[c] - lv.v[c];
-                const R dmv = mu_.v[c] - mv.v[c];
-                const R d1v = pu.v[c] - pv.v[c];
-                const R b1 = b - dmv;                   // b_{m-1}
-                const R b2 = b1 - d1v;                  // b_{m-2}
-                const R Dd = dmv - beta * d1v;          // delta_i - delta_j
-                const R vmb = -Dd - (ta * b1 - tb * b2);
-                sb += b * b;
-                sv += vmb * vmb;
+                for (int c = 0; c < C; ++c) {
+                    R b1 = a.v[c] - bj.v[c];
+                    if constexpr (FF) b1 += al.v[c] - lj.v[c];
+                    const R d1v = d1.v[c] - d1j.v[c];
+                    const R dmv = d0.v[c] - d0j.v[c];
+                    const R b = b1 + dmv;                   // b_m
+                    const R b2 = b1 - d1v;                  // b_{m-2}
+                    const R Dd = dmv - beta * d1v;          // delta_i - delta_j
+                    const R vmb = -Dd - (ta * b1 - tb * b2);
+                    sb += b * b;
+                    sv += vmb * vmb;
+                }
+                sNb[e] += (float)sb;     // edge e lies in exactly one work item
+                f_vb += (float)sv;
             }
-            sNb[e] += (double)sb;
-            s_vb += (double)sv;
         }
+        s_ua += f_ua;
+        s_vb += f_vb;
+        s_rs += f_rs;
+        s_st += f_st;
+        s_na += f_na;
+        s_nz += f_nz;
+        s_dl += f_dl;
         __syncthreads();
+        cur ^= (PREF ? 1 : 0);
     }
 
     // ---- partials of this CTA
@@ -280,74 +475,103 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
 }
 
 // ------------------------------------------------------------------ reduce
+// Block = 32 edges x 8 CTA groups.  Each edge's partials are summed in a fixed
+// order (CTA group, then group index), so results do not depend on timing.
+constexpr int kRedEdges = 32;
+constexpr int kRedGroups = kReduceThreads / kRedEdges;
+
 template <typename R>
 __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R> P) {
     PdState* st = P.st;
     if (st->done) return;
     __shared__ double s_d;
-    __shared__ double red[32];
+    __shared__ double part[kRedGroups][kRedEdges];
     __shared__ bool s_last;
     const int G = P.G, m = P.m, tid = threadIdx.x;
-    if (tid == 0) {
+    if (tid < 32) {
+        // d_m (Eq. 5): lane-strided partial sums, then a fixed shuffle tree
         double acc = 0.0;
-        for (int g = 0; g < G; ++g)
+        for (int g = tid; g < G; g += 32)
             acc += P.Ps[(size_t)g * kNumScalarPartials + kPsUA] + P.Ps[(size_t)g * kNumScalarPartials + kPsVB];
-        s_d = sqrt(acc + st->eps);            // d_m (Eq. 5)
+        acc = warp_sum(acc);
+        if (tid == 0) s_d = sqrt(acc + st->eps);
     }
+    const int lane = tid % kRedEdges, grp = tid / kRedEdges;
+    const int e = blockIdx.x * kRedEdges + lane;
+    double s = 0.0;
+    if (e < m)
+        for (int g = grp; g < G; g += kRedGroups) s += (double)P.Pnb[(size_t)g * m + e];
+    part[grp][lane] = s;
     __syncthreads();
     const double d = s_d;
-    const double gamma = st->gamma, rho = st->rho;
-    R* tout = P.t[st->par ^ 1];              // t_{m+1} replaces t_{m-1}
-    double cnt = 0.0;
-    unsigned long long hsh = 0ULL;
-    for (int e = blockIdx.x * blockDim.x + tid; e < m; e += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int g = 0; g < G; ++g) s += P.Pnb[(size_t)g * m + e];
-        const double nb = sqrt(s);
-        const double lhs = gamma * P.w[e] * d;
-        const double rhs = rho * nb;
-        const bool fz = lhs >= rhs;          // prox returns exactly zero
-        tout[e] = fz ? (R)1 : (R)(lhs / rhs);
-        P.nb[e] = nb;
-        P.fused[e] = fz ? 1 : 0;
-        if (fz) {
-            cnt += 1.0;
-            hsh += mix64((unsigned long long)e + 1ULL);
+    if (grp == 0) {
+        const double gamma = st->gamma, rho = st->rho;
+        const R* tin = P.t[st->par];
+        R* tout = P.t[st->par ^ 1];          // (t_{m+1}, t_m) replaces (t_m, t_{m-1})
+        bool fz = false;
+        unsigned long long h = 0ULL;
+        if (e < m) {
+            double tot = 0.0;
+            for (int g = 0; g < kRedGroups; ++g) tot += part[g][lane];
+            const double nb = sqrt(tot);
+            const double lhs = gamma * P.w[e] * d;
+            const double rhs = rho * nb;
+            fz = lhs >= rhs;                 // the prox returns exactly zero
+            const int qa = P.qpos[2 * e], qb = P.qpos[2 * e + 1];
+            const R tnew = fz ? (R)1 : (R)(lhs / rhs);
+            const R told = tin[2 * qa];
+            tout[2 * qa] = tnew;
+            tout[2 * qa + 1] = told;
+            tout[2 * qb] = tnew;
+            tout[2 * qb + 1] = told;
+            P.nb[e] = nb;
+            P.fused[e] = fz ? 1 : 0;
+            if (fz) h = mix64((unsigned long long)e + 1ULL);
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, fz);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+        if (lane == 0) {
+            P.Rf[2 * blockIdx.x] = (unsigned long long)__popc(ballot);
+            P.Rf[2 * blockIdx.x + 1] = h;
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&st->counter, 1u);
+            s_last = (ticket == gridDim.x - 1);
         }
     }
-    // fused count is exact in double; the hash is summed with wrap-around
-    const double bc = block_sum(cnt, red);
-    __shared__ unsigned long long sh[kReduceThreads];
-    sh[tid] = hsh;
     __syncthreads();
-    if (tid == 0) {
-        unsigned long long hb = 0ULL;
-        for (int k = 0; k < blockDim.x; ++k) hb += sh[k];
-        P.Rf[2 * blockIdx.x] = (unsigned long long)bc;
-        P.Rf[2 * blockIdx.x + 1] = hb;
-        __threadfence();
-        const unsigned int ticket = atomicAdd(&st->counter, 1u);
-        s_last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last || tid != 0) return;
+    if (!s_last) return;
     __threadfence();
 
-    // ---- last block: scalar state update (serial, fixed order)
-    unsigned long long nf = 0ULL, hash = 0ULL;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-        nf += P.Rf[2 * b];
-        hash += P.Rf[2 * b + 1];
+    // ---- last block: scalar state update (block-parallel fixed-order sums, then thread 0)
+    const double rho = st->rho;
+    unsigned long long nf_l = 0ULL, hash_l = 0ULL;
+    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+        nf_l += P.Rf[2 * b];
+        hash_l += P.Rf[2 * b + 1];
     }
-    double rs = 0.0, stp = 0.0, na = 0.0, nzs = 0.0, dls = 0.0;
-    for (int g = 0; g < G; ++g) {
+    double q_rs = 0.0, q_st = 0.0, q_na = 0.0, q_nz = 0.0, q_dl = 0.0;
+    for (int g = tid; g < G; g += blockDim.x) {
         const double* ps = P.Ps + (size_t)g * kNumScalarPartials;
-        rs += ps[kPsRestart];
-        stp += ps[kPsStep];
-        na += ps[kPsNormA];
-        nzs += ps[kPsNoise];
-        dls += ps[kPsDelta];
+        q_rs += ps[kPsRestart];
+        q_st += ps[kPsStep];
+        q_na += ps[kPsNormA];
+        q_nz += ps[kPsNoise];
+        q_dl += ps[kPsDelta];
     }
+    __shared__ double red[32];
+    const double rs = block_sum(q_rs, red);
+    const double stp = block_sum(q_st, red);
+    const double na = block_sum(q_na, red);
+    const double nzs = block_sum(q_nz, red);
+    const double dls = block_sum(q_dl, red);
+    const unsigned long long nf = (unsigned long long)block_sum((double)nf_l, red);
+    __shared__ unsigned long long hsh[kReduceThreads];
+    hsh[tid] = hash_l;
+    __syncthreads();
+    if (tid != 0) return;
+    unsigned long long hash = 0ULL;
+    for (int k = 0; k < (int)blockDim.x; ++k) hash += hsh[k];
     const double unit = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     const double noise = unit * sqrt(nzs);
     st->iter += 1;
@@ -440,9 +664,13 @@ __global__ void pd_init_kernel(IterParams<R> P, const R* Y0, size_t total) {
             P.Em[k] = (R)0;
         }
     }
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * (size_t)P.m; q += (size_t)gridDim.x * blockDim.x) {
+        P.t[0][2 * q] = (R)1;   // t = 1 - s with s = 0: V_0 = 0 (and V_{-1} = 0)
+        P.t[0][2 * q + 1] = (R)1;
+        P.t[1][2 * q] = (R)1;
+        P.t[1][2 * q + 1] = (R)1;
+    }
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)P.m; e += (size_t)gridDim.x * blockDim.x) {
-        P.t[0][e] = (R)1;   // t = 1 - s with s = 0: V_0 = 0
-        P.t[1][e] = (R)1;
         P.nb[e] = 0.0;
         P.fused[e] = 0;
     }
@@ -509,9 +737,9 @@ __global__ void pd_finalize_kernel(IterParams<R> P, float* U_out, int64_t ld_out
     }
 }
 
-template <typename R>
+template <typename R, bool PREF>
 cudaError_t launch_slice(const IterParams<R>& P, size_t smem, cudaStream_t s) {
-    auto kern = pd_slice_kernel<R>;
+    auto kern = pd_slice_kernel<R, PREF>;
     // The shared-memory opt-in is a function attribute, not a stream
     // operation: it is raised once, to the device maximum, on the first
     // (uncaptured) launch so that launches inside graph capture need no call.
@@ -534,29 +762,43 @@ cudaError_t launch_slice(const IterParams<R>& P, size_t smem, cudaStream_t s) {
 
 }  // namespace
 
-size_t pd_slice_smem_bytes(int n, int m, bool fp64) {
-    const size_t rows = fp64 ? (size_t)n * 4 * C * sizeof(double) : (size_t)n * 6 * C * sizeof(float);
-    return rows + (size_t)m * sizeof(double);
+size_t pd_slice_smem_bytes(int n, int m, int nch, int ech, bool fp64, bool prefetch) {
+    return fp64 ? SliceLayout<double>::bytes(n, m, nch, ech, prefetch)
+                : SliceLayout<float>::bytes(n, m, nch, ech, prefetch);
 }
 
-int reduce_blocks(int m) {
-    int b = (m + kReduceThreads - 1) / kReduceThreads;
-    if (b < 1) b = 1;
-    if (b > 128) b = 128;
-    return b;
+constexpr size_t kPrefetchSmemMax = 160 * 1024;
+
+int pd_reduce_blocks(int m) { return m > 0 ? (m + kRedEdges - 1) / kRedEdges : 1; }
+
+// largest dynamic shared memory a block may use on this device (static part excluded)
+static size_t slice_smem_limit() {
+    static int lim = 0;
+    if (!lim) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        lim = optin - 2048;
+    }
+    return (size_t)lim;
 }
 
 template <typename R>
 cudaError_t launch_pd_slice(const IterParams<R>& P, cudaStream_t s) {
-    const size_t smem = pd_slice_smem_bytes(P.n, P.m, std::is_same<R, double>::value);
+    constexpr bool fp64 = std::is_same<R, double>::value;
     count_launches(1);
-    return launch_slice<R>(P, smem, s);
+    // the double buffer is worth it only while at least ~96 KB of the SM's
+    // 256 KB L1/shared array stays L1 for the per-edge weights and row loads
+    const size_t with_pref = pd_slice_smem_bytes(P.n, P.m, P.nch, P.ech, fp64, true);
+    if (with_pref <= slice_smem_limit() && with_pref <= kPrefetchSmemMax)
+        return launch_slice<R, true>(P, with_pref, s);
+    return launch_slice<R, false>(P, pd_slice_smem_bytes(P.n, P.m, P.nch, P.ech, fp64, false), s);
 }
 
 template <typename R>
 cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s) {
     count_launches(1);
-    pd_reduce_kernel<R><<<reduce_blocks(P.m), kReduceThreads, 0, s>>>(P);
+    pd_reduce_kernel<R><<<pd_reduce_blocks(P.m), kReduceThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 
