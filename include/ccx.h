@@ -151,6 +151,33 @@ ccx_status ccx_get_edges(const ccx_problem* pr, int64_t* n_edges, int32_t* ei, i
 ccx_status ccx_fusion_scale(const ccx_problem* pr, double* gamma0);
 
 /*
+ * The same value as ccx_fusion_scale, computed without allocating memory: no
+ * device memory at all, and no host memory unless the call fails (the error
+ * message).  The paper has no counterpart to this call.  It serves callers
+ * that may not allocate at the moment they need the gamma scale: a service
+ * whose device memory is all reserved by its own pool, where cudaMalloc would
+ * fail, or a loop that cannot afford the device-wide synchronisation that
+ * cudaFree implies.  ccx_fusion_scale takes a temporary device buffer of 8
+ * bytes per edge; this call uses a fixed buffer compiled into the library
+ * instead (8 MiB of device memory, plus a host array of the same size).
+ *   Limit   : at most 1048576 (2^20) edges; a larger edge set returns
+ *             CCX_EINVAL with a message saying so (ccx_fusion_scale still
+ *             handles it).
+ *   Set-up  : the first call on a device looks up the buffer's address on
+ *             that device and keeps it; make that first call before any
+ *             stream capture begins on the device.
+ *   Sharing : every call in the process uses the same two buffers, which keep
+ *             the last call's per-edge ratios.  A call writes every entry it
+ *             reads, so nothing has to be cleared first.  Two calls whose GPU
+ *             work overlapped would race on the device buffer; a call
+ *             therefore holds a process-wide lock until its GPU work has
+ *             finished, and calls from several host threads run one after
+ *             another.
+ * Returns CCX_EINVAL without edges.
+ */
+ccx_status ccx_fusion_scale_noalloc(const ccx_problem* pr, double* gamma0);
+
+/*
  * Solve the warm-started path over gammas[0..n_gamma-1] in the order given
  * (Evaluation of Clusters: the program minimises over a user-given grid of mu).
  *   gammas    : host array, each finite and >= 0.

@@ -54,6 +54,7 @@ _sigs = {
     "ccx_build_knn": (C.c_int, [_P, C.POINTER(KnnRule)]),
     "ccx_get_edges": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P]),
     "ccx_fusion_scale": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "ccx_fusion_scale_noalloc": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
     "ccx_reset_path": (C.c_int, [_P]),
     "ccx_problem_destroy": (C.c_int, [_P]),
@@ -159,6 +160,13 @@ def get_edges(h):
 def fusion_scale(h) -> float:
     g = C.c_double(0.0)
     _check(_lib.ccx_fusion_scale(h, C.byref(g)))
+    return g.value
+
+
+def fusion_scale_noalloc(h) -> float:
+    """ccx_fusion_scale through the library's fixed buffers: no memory is allocated."""
+    g = C.c_double(0.0)
+    _check(_lib.ccx_fusion_scale_noalloc(h, C.byref(g)))
     return g.value
 
 

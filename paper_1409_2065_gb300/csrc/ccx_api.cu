@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -723,6 +724,39 @@ ccx_status ccx_fusion_scale(const ccx_problem* pr_c, double* gamma0) {
     std::sort(h.begin(), h.end());
     *gamma0 = (m % 2) ? h[m / 2] : 0.5 * (h[m / 2 - 1] + h[m / 2]);
     return leave(pr);
+}
+
+namespace {
+// host copy of the per-edge ratios for the allocation-free variant below
+double g_ratio_host[kStaticEdgesMax];
+std::mutex g_ratio_mu;
+}  // namespace
+
+ccx_status ccx_fusion_scale_noalloc(const ccx_problem* pr_c, double* gamma0) {
+    g_err.clear();
+    ccx_problem* pr = const_cast<ccx_problem*>(pr_c);
+    if (!pr || !gamma0) return fail(CCX_EINVAL, "NULL argument");
+    const int64_t m = (int64_t)pr->ei.size();
+    if (m == 0) return fail(CCX_EINVAL, "no edges");
+    if (m > kStaticEdgesMax)
+        return fail(CCX_EINVAL, "ccx_fusion_scale_noalloc handles at most %d edges, this problem has %lld; "
+                                "use ccx_fusion_scale", kStaticEdgesMax, (long long)m);
+    std::lock_guard<std::mutex> lk(g_ratio_mu);
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    double* scratch = nullptr;
+    CUDA_TRY(static_edge_scratch(&scratch));
+    CUDA_TRY(edge_ratios_static(pr->Y0f, (int)pr->p, pr->ld, pr->d_ei, pr->d_ej, pr->d_w, (int)m, scratch, pr->work));
+    CUDA_TRY(cudaMemcpyAsync(g_ratio_host, scratch, sizeof(double) * m, cudaMemcpyDeviceToHost, pr->work));
+    s = leave(pr);
+    if (s != CCX_OK) return s;
+    // median without a sort buffer: the upper middle by selection, the lower
+    // middle (even m) as the largest element left of it
+    double* h = g_ratio_host;
+    std::nth_element(h, h + m / 2, h + m);
+    const double hi = h[m / 2];
+    *gamma0 = (m % 2) ? hi : 0.5 * (*std::max_element(h, h + m / 2) + hi);
+    return CCX_OK;
 }
 
 ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts, float* U_out,

@@ -135,6 +135,13 @@ cudaError_t launch_fill_missing(const float* Xf, const double* Xd, const uint32_
 cudaError_t launch_fused_labels(int n, int m, const int* ei, const int* ej, const uint8_t* fused,
                                 int* labels, int* n_clusters, int* scratch, cudaStream_t s);
 
+// per-edge fusion ratios into the library's fixed device buffer (static_scratch.cu)
+constexpr int kStaticEdgesMax = 1 << 20;   // 8 MiB of doubles per device
+// device address of the buffer on the current device (looked up once per device)
+cudaError_t static_edge_scratch(double** out);
+cudaError_t edge_ratios_static(const float* Y0f, int p, int ld, const int* ei_d, const int* ej_d, const double* w_d,
+                               int m, double* scratch, cudaStream_t s);
+
 // kNN weights (knn_kernels.cu)
 struct KnnResult {
     std::vector<int> ei, ej;
