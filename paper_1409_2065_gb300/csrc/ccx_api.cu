@@ -100,12 +100,14 @@ struct ccx_problem {
     int* d_ej = nullptr;
     double* d_w = nullptr;
     int* d_rowptr = nullptr;
-    int* d_nc0 = nullptr;
-    uint16_t* d_csr = nullptr;
-    int* d_qpos = nullptr;
-    uint2* d_nchunk = nullptr;
-    uint4* d_echunk = nullptr;
-    int nch = 0, ech = 0;
+    int* d_erow = nullptr;
+    int* d_ps0 = nullptr;
+    uint16_t* d_csrT = nullptr;
+    uint16_t* d_ejT = nullptr;
+    uint2* d_thrA = nullptr;
+    int* d_thrE = nullptr;
+    int2* d_posA = nullptr;
+    int la = 1, le = 1, nslots = 0;
     // path state
     void* A[2] = {nullptr, nullptr};
     float* Alo[2] = {nullptr, nullptr};
@@ -177,16 +179,17 @@ void free_edges(ccx_problem* pr) {
     cudaFree(pr->d_ej);
     cudaFree(pr->d_w);
     cudaFree(pr->d_rowptr);
-    cudaFree(pr->d_nc0);
-    cudaFree(pr->d_csr);
-    cudaFree(pr->d_qpos);
-    pr->d_qpos = nullptr;
-    cudaFree(pr->d_nchunk);
-    cudaFree(pr->d_echunk);
-    pr->d_ei = pr->d_ej = pr->d_rowptr = pr->d_nc0 = nullptr;
-    pr->d_csr = nullptr;
-    pr->d_nchunk = nullptr;
-    pr->d_echunk = nullptr;
+    cudaFree(pr->d_erow);
+    cudaFree(pr->d_ps0);
+    cudaFree(pr->d_csrT);
+    cudaFree(pr->d_ejT);
+    cudaFree(pr->d_thrA);
+    cudaFree(pr->d_thrE);
+    cudaFree(pr->d_posA);
+    pr->d_ei = pr->d_ej = pr->d_rowptr = pr->d_erow = pr->d_ps0 = pr->d_thrE = nullptr;
+    pr->d_csrT = pr->d_ejT = nullptr;
+    pr->d_thrA = nullptr;
+    pr->d_posA = nullptr;
     pr->d_w = nullptr;
 }
 
@@ -272,65 +275,77 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
         ent[fillp[pr->ei[q]]++] = {pr->ej[q], q};
         ent[fillp[pr->ej[q]]++] = {pr->ei[q], q};
     }
-    // entries: neighbour index; rowmid[i] = first entry with neighbour > i; qpos: the two
-    // CSR positions of each edge (its entry in the smaller endpoint's row, then the larger's)
+    // rows by increasing neighbour; qa/qb: CSR position of edge e in the row of ei / ej
     std::vector<uint16_t> csr(2 * (size_t)m);
-    std::vector<int> rowmid(n, 0), qpos(2 * (size_t)m, 0);
+    std::vector<int> qa(m), qb(m), rowof(2 * (size_t)m);
     for (int64_t i = 0; i < n; ++i) {
         std::sort(ent.begin() + rowptr[i], ent.begin() + rowptr[i + 1]);
-        rowmid[i] = rowptr[i + 1];
-        for (int k = rowptr[i + 1] - 1; k >= rowptr[i]; --k)
-            if (ent[k].first > i) rowmid[i] = k;
         for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
             csr[k] = (uint16_t)ent[k].first;
-            const int e = ent[k].second;
-            qpos[2 * (size_t)e + (ent[k].first > i ? 0 : 1)] = k;
+            rowof[k] = (int)i;
+            (ent[k].first > i ? qa : qb)[ent[k].second] = k;
         }
     }
-    // work items of the iteration kernel: runs of <= kChunk CSR entries of one node
-    // (all neighbours for the node phase; the larger-index ones for the edge phase)
-    std::vector<uint2> nchunk;
-    std::vector<uint4> echunk;
-    std::vector<int> nc0(n + 1, 0);
-    for (int64_t i = 0; i < n; ++i) {
-        nc0[i] = (int)nchunk.size();
-        for (int q = rowptr[i]; q < rowptr[i + 1]; q += kChunk)
-            nchunk.push_back(make_uint2((uint32_t)q, (uint32_t)i | ((uint32_t)std::min(kChunk, rowptr[i + 1] - q) << 16)));
-        for (int q = rowmid[i]; q < rowptr[i + 1]; q += kChunk) {
-            // edges are sorted by (i, j): the entries of row i with j > i are edges
-            // ebase, ebase + 1, ... in order
-            const int e = ent[q].second;
-            echunk.push_back(make_uint4((uint32_t)q, (uint32_t)i | ((uint32_t)std::min(kChunk, rowptr[i + 1] - q) << 16),
-                                        (uint32_t)e, 0u));
-        }
+    // equal runs of the two sweeps, one per thread of the iteration kernel
+    const int T = kSliceThreads;
+    const int64_t m2 = 2 * (int64_t)m;
+    const int la = (int)std::max<int64_t>(1, (m2 + T - 1) / T);
+    const int le = std::max(1, (m + T - 1) / T);
+    auto posA = [&](int64_t q) { return (int)((q % la) * T + q / la); };
+    std::vector<uint16_t> csrT((size_t)la * T, 0), ejT((size_t)le * T, 0);
+    for (int64_t q = 0; q < m2; ++q) csrT[posA(q)] = csr[q];
+    for (int e = 0; e < m; ++e) ejT[(size_t)(e % le) * T + e / le] = (uint16_t)pr->ej[e];
+    // node-sweep partial slots: one per (run, row) overlap, numbered in entry
+    // order, so the slots of a node are consecutive
+    std::vector<uint2> thrA(T);
+    std::vector<int> ps0(n + 1, 0);
+    int nslots = 0;
+    for (int t = 0; t < T; ++t) {
+        const int64_t q0 = (int64_t)t * la, q1 = std::min<int64_t>(q0 + la, m2);
+        thrA[t] = make_uint2(q0 < q1 ? (uint32_t)rowof[q0] : 0u, (uint32_t)nslots);
+        for (int64_t q = q0; q < q1; ++q)
+            if (q == q0 || rowof[q] != rowof[q - 1]) {
+                ps0[rowof[q] + 1]++;
+                ++nslots;
+            }
     }
-    nc0[n] = (int)nchunk.size();
+    for (int64_t i = 0; i < n; ++i) ps0[i + 1] += ps0[i];
+    std::vector<int> erow(n + 1, 0), thrE(T, 0);
+    for (int e = 0; e < m; ++e) erow[pr->ei[e] + 1]++;
+    for (int64_t i = 0; i < n; ++i) erow[i + 1] += erow[i];
+    for (int t = 0; t < T; ++t)
+        if ((int64_t)t * le < m) thrE[t] = pr->ei[(size_t)t * le];
+    std::vector<int2> posE((size_t)le * T, make_int2(0, 0));
+    for (int e = 0; e < m; ++e) posE[(size_t)(e % le) * T + e / le] = make_int2(posA(qa[e]), posA(qb[e]));
     free_path(pr);
     free_edges(pr);
+    pr->la = la;
+    pr->le = le;
+    pr->nslots = nslots;
     CUDA_TRY(dalloc(&pr->d_ei, m));
     CUDA_TRY(dalloc(&pr->d_ej, m));
     CUDA_TRY(dalloc(&pr->d_w, m));
     CUDA_TRY(dalloc(&pr->d_rowptr, n + 1));
-    CUDA_TRY(dalloc(&pr->d_nc0, n + 1));
-    CUDA_TRY(dalloc(&pr->d_csr, 2 * (size_t)m));
-    CUDA_TRY(dalloc(&pr->d_qpos, 2 * (size_t)m));
-    CUDA_TRY(dalloc(&pr->d_nchunk, nchunk.size()));
-    CUDA_TRY(dalloc(&pr->d_echunk, echunk.size()));
-    pr->nch = (int)nchunk.size();
-    pr->ech = (int)echunk.size();
-    if (!nchunk.empty())
-        CUDA_TRY(cudaMemcpy(pr->d_nchunk, nchunk.data(), sizeof(uint2) * nchunk.size(), cudaMemcpyHostToDevice));
-    if (!echunk.empty())
-        CUDA_TRY(cudaMemcpy(pr->d_echunk, echunk.data(), sizeof(uint4) * echunk.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(dalloc(&pr->d_erow, n + 1));
+    CUDA_TRY(dalloc(&pr->d_ps0, n + 1));
+    CUDA_TRY(dalloc(&pr->d_csrT, csrT.size()));
+    CUDA_TRY(dalloc(&pr->d_ejT, ejT.size()));
+    CUDA_TRY(dalloc(&pr->d_thrA, T));
+    CUDA_TRY(dalloc(&pr->d_thrE, T));
+    CUDA_TRY(dalloc(&pr->d_posA, posE.size()));
     if (m > 0) {
         CUDA_TRY(cudaMemcpy(pr->d_ei, pr->ei.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(pr->d_ej, pr->ej.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(pr->d_w, pr->w.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(pr->d_csr, csr.data(), sizeof(uint16_t) * 2 * m, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(pr->d_qpos, qpos.data(), sizeof(int) * 2 * m, cudaMemcpyHostToDevice));
     }
+    CUDA_TRY(cudaMemcpy(pr->d_csrT, csrT.data(), sizeof(uint16_t) * csrT.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_ejT, ejT.data(), sizeof(uint16_t) * ejT.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_thrA, thrA.data(), sizeof(uint2) * T, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_thrE, thrE.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_posA, posE.data(), sizeof(int2) * posE.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pr->d_rowptr, rowptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(pr->d_nc0, nc0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_erow, erow.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_ps0, ps0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     return CCX_OK;
 }
 
@@ -348,13 +363,16 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.Q = reinterpret_cast<R*>(pr->Q);
     P.Em = reinterpret_cast<R*>(pr->Em);
     P.rowptr = pr->d_rowptr;
-    P.csr = pr->d_csr;
-    P.qpos = pr->d_qpos;
-    P.nchunk = pr->d_nchunk;
-    P.echunk = pr->d_echunk;
-    P.nc0 = pr->d_nc0;
-    P.nch = pr->nch;
-    P.ech = pr->ech;
+    P.erow = pr->d_erow;
+    P.ps0 = pr->d_ps0;
+    P.csrT = pr->d_csrT;
+    P.ejT = pr->d_ejT;
+    P.thrA = pr->d_thrA;
+    P.thrE = pr->d_thrE;
+    P.posA = pr->d_posA;
+    P.la = pr->la;
+    P.le = pr->le;
+    P.nslots = pr->nslots;
     P.ei = pr->d_ei;
     P.ej = pr->d_ej;
     P.w = pr->d_w;
@@ -375,16 +393,16 @@ IterParams<R> make_params(ccx_problem* pr) {
 
 ccx_status check_limits(ccx_problem* pr) {
     const int m = (int)pr->ei.size();
-    if (pr->n > 65535 || m > 65535)
-        return fail(CCX_EUNSUPPORTED, "the iteration kernel packs node and edge indices in 16 bits: n and the "
-                                      "number of edges must be <= 65535 (have %lld, %d)", (long long)pr->n, m);
+    if (pr->n > 65535)
+        return fail(CCX_EUNSUPPORTED, "the iteration kernel stores node indices in 16 bits: n must be <= 65535 "
+                                      "(have %lld)", (long long)pr->n);
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pr->device));
-    const size_t need = pd_slice_smem_bytes((int)pr->n, m, pr->nch, pr->ech, pr->precision == CCX_FP64, false);
+    const size_t need = pd_slice_smem_bytes((int)pr->n, pr->la, pr->le, pr->nslots, pr->precision == CCX_FP64, false);
     if (need + 2048 > (size_t)optin)
         return fail(CCX_EUNSUPPORTED,
                     "n = %lld cases and %d edges need %zu bytes of shared memory per block (a column slice of "
-                    "all rows plus 12 bytes per edge); the device allows %d",
+                    "all rows plus ~10 bytes per edge); the device allows %d",
                     (long long)pr->n, m, need, optin);
     return CCX_OK;
 }
@@ -401,17 +419,18 @@ ccx_status ensure_path(ccx_problem* pr) {
         CUDA_TRY(cudaMalloc(&pr->A[k], es * nl));
         CUDA_TRY(cudaMalloc(&pr->Dl[k], es * nl));
         if (!fp64) CUDA_TRY(dalloc(&pr->Alo[k], nl));
-        CUDA_TRY(cudaMalloc(&pr->t[k], es * 4 * std::max(m, 1)));   // a (t, t_prev) pair per CSR entry
+        // a (t, t_prev) pair per node-sweep and per edge-sweep position
+        CUDA_TRY(cudaMalloc(&pr->t[k], es * 2 * ((size_t)pr->la + pr->le) * kSliceThreads));
     }
     if (pr->has_mask) {
         CUDA_TRY(cudaMalloc(&pr->Q, es * nl));
         CUDA_TRY(cudaMalloc(&pr->Em, es * nl));
     }
-    CUDA_TRY(dalloc(&pr->Pnb, (size_t)pr->G * std::max(m, 1)));
+    CUDA_TRY(dalloc(&pr->Pnb, (size_t)pr->G * pr->le * kSliceThreads));
     CUDA_TRY(dalloc(&pr->Ps, (size_t)pr->G * kNumScalarPartials));
     CUDA_TRY(dalloc(&pr->nb, m));
     CUDA_TRY(dalloc(&pr->fused, m));
-    CUDA_TRY(dalloc(&pr->Rf, 2 * (size_t)pd_reduce_blocks(m)));
+    CUDA_TRY(dalloc(&pr->Rf, 2 * (size_t)pd_reduce_blocks(pr->le)));
     CUDA_TRY(dalloc(&pr->st, 1));
     CUDA_TRY(cudaMallocHost(&pr->st_host, 2 * sizeof(PdState)));
     CUDA_TRY(dalloc(&pr->Ustage, (size_t)pr->n * pr->p));

@@ -23,7 +23,6 @@ namespace ccx {
 
 constexpr int kSliceThreads = 512;   // threads of the fused iteration kernel
 constexpr int kSliceCols = 4;        // columns per staged slice (one 16-byte vector for float)
-constexpr int kChunk = 16;           // neighbours per work item of the iteration kernel
 constexpr int kReduceThreads = 256;
 constexpr int kConvWindow = 64;      // iterations per convergence window
 constexpr int kRateWindows = 8;      // windows spanned by the contraction-rate estimate
@@ -83,24 +82,33 @@ struct IterParams {
     R* Dl[2];                   // velocity slots Delta = A_m - A_{m-1}
     R* Q;                       // missing entries: U_y - A of the last iteration
     R* Em;                      // missing entries: U - A_prev of the last iteration
-    R* t[2];                    // per CSR entry, interleaved (t_m, t_{m-1}) of its edge, t = 1 - s
+    // The two edge sweeps of the iteration kernel are split into equal runs,
+    // one per thread: thread t takes node-sweep entries (CSR positions over
+    // both directions) [t*la, (t+1)*la) and edge-sweep entries (edge ids in
+    // (i, j) order) [t*le, (t+1)*le).  Per-entry arrays of a sweep store the
+    // k-th entry of thread t at k*T + t (T = kSliceThreads), so a warp's k-th
+    // step reads consecutive words.
+    R* t[2];                    // (t_m, t_{m-1}) pairs, t = 1 - s: la*T pairs in node-sweep
+                                // order, then le*T pairs in edge-sweep order
     const int* rowptr;          // CSR over both directions, n + 1
-    const uint16_t* csr;        // CSR entries: neighbour index
-    const int* qpos;            // per edge: its two CSR positions (from the smaller, then the larger endpoint)
-    const uint2* nchunk;        // node-phase work items: (first CSR entry, node | length << 16)
-    const uint4* echunk;        // edge-phase work items over the entries with a larger neighbour:
-                                // (first CSR entry, node | length << 16, first edge id, 0)
-    const int* nc0;             // n + 1: first node-phase work item of each node
+    const int* erow;            // n + 1: first edge whose smaller endpoint is i
+    const int* ps0;             // n + 1: first node-sweep partial slot of node i
+    const uint16_t* csrT;       // la*T: neighbour of each node-sweep entry
+    const uint16_t* ejT;        // le*T: larger endpoint of each edge-sweep entry
+    const uint2* thrA;          // T: (node of the first entry, first partial slot) of each node-sweep run
+    const int* thrE;            // T: smaller endpoint of the first edge of each edge-sweep run
+    const int2* posA;           // le*T: node-sweep positions of the edge at each edge-sweep position
     const int* ei;              // edge endpoints, i < j
     const int* ej;
     const double* w;            // edge weights
-    float* Pnb;                 // per-CTA per-edge partial ||b||^2, G x m
+    float* Pnb;                 // per-CTA per-edge partial ||b||^2, G x le*T (edge-sweep order)
     double* Ps;                 // per-CTA scalar partials, G x kNumScalarPartials
     double* nb;                 // per-edge ||b_m|| of the last iteration
     uint8_t* fused;             // per-edge fused flag of t_{m+1}
     unsigned long long* Rf;     // per reduce-block fused count / hash
     PdState* st;
-    int n, ld, ldw, m, nslices, G, nch, ech;
+    int n, ld, ldw, m, nslices, G;
+    int la, le, nslots;         // run lengths of the two sweeps; node-sweep partial slots
 };
 
 // ---------------------------------------------------------------- launchers
@@ -120,8 +128,8 @@ cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s);
 void count_launches(unsigned long long k);
 template <typename R>
 cudaError_t launch_pd_finalize(const IterParams<R>& P, float* U_out, int64_t ld_out, int p, cudaStream_t s);
-size_t pd_slice_smem_bytes(int n, int m, int nch, int ech, bool fp64, bool prefetch);
-int pd_reduce_blocks(int m);
+size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch);
+int pd_reduce_blocks(int le);
 
 // data preparation (prep_kernels.cu)
 cudaError_t launch_pack_input(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld_in,

@@ -117,28 +117,27 @@ __device__ __forceinline__ void copy_vec_async(T* dst, const T* src) {
 
 // Shared-memory layout of the iteration kernel (all offsets multiples of 16 bytes):
 //   per staging buffer b in {0, 1 (prefetch only)}:
-//       A_hi[n], (A_lo[n] on the FP32 path), Delta_{m-1}[n], X[n], mask word[n]
+//       A_hi[n], (A_lo[n] on the FP32 path), Delta_{m-1}[n], X[n], mask word[n] (padded)
 //   Delta_m[n]
-//   Gpart[nchunks]               (partial correction sums of the node-phase work items)
-//   echunk[echunks]              (edge work items: first entry, node | length << 16, first edge, 0)
-//   nchunk[nchunks]              (node work items: first entry, node | length << 16)
-//   rowptr[n + 1], nc0[n + 1]    (nc0[i]: first node-phase work item of node i)
-//   nbacc[m]                     (float: this CTA's sum of ||b_m||^2 over its slices)
-//   csr[2 m]                     (uint16 neighbour index)
+//   Gpart[nslots]                (partial correction sums of the node-sweep runs)
+//   rowptr[n + 1], erow[n + 1], ps0[n + 1]
+//   nbacc[le*T]                  (float: this CTA's sum of ||b_m||^2 over its slices)
+//   csrT[la*T], ejT[le*T]        (uint16 neighbour indices of the two sweeps)
 template <typename R>
 struct SliceLayout {
     static constexpr bool FF = std::is_same<R, float>::value;
     static constexpr size_t row = sizeof(R) * C;             // bytes of one row slice
-    // A_hi (+A_lo) + Delta_{m-1} + X + mask word (padded to 16 bytes)
-    static constexpr size_t buf = (FF ? 4 : 3) * row + 16;
-    static size_t bytes(int n, int m, int nch, int ech, bool pref) {
-        size_t b = (pref ? 2 : 1) * buf * (size_t)n + row * (size_t)n;
-        b += row * (size_t)nch;
-        b += sizeof(uint4) * (size_t)ech + sizeof(uint2) * (size_t)nch;
-        b += sizeof(int) * 2 * (size_t)(n + 1);
+    __host__ __device__ static size_t mask_bytes(int n) { return ((size_t)n * 4 + 15) / 16 * 16; }
+    // A_hi (+A_lo) + Delta_{m-1} + X, then the mask words
+    static size_t buf(int n) { return (FF ? 4 : 3) * row * (size_t)n + mask_bytes(n); }
+    static size_t bytes(int n, int la, int le, int nslots, bool pref) {
+        const size_t LA = (size_t)la * kSliceThreads, LE = (size_t)le * kSliceThreads;
+        size_t b = (pref ? 2 : 1) * buf(n) + row * (size_t)n;
+        b += row * (size_t)nslots;
+        b += sizeof(int) * 3 * (size_t)(n + 1);
         b = (b + 15) / 16 * 16;
-        b += sizeof(float) * (size_t)m;
-        b += sizeof(uint16_t) * 2 * (size_t)m;
+        b += sizeof(float) * LE;
+        b += sizeof(uint16_t) * (LA + LE);
         return (b + 15) / 16 * 16;
     }
 };
@@ -151,8 +150,14 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     const PdState* st = P.st;
     if (st->done) return;
 
+    constexpr int T = kSliceThreads;
     const int n = P.n, ld = P.ld, m = P.m, tid = threadIdx.x, G = gridDim.x;
-    const int nch = P.nch, ech = P.ech;
+    const int la = P.la, le = P.le, LA = la * T, LE = le * T;
+    // this thread's runs of the node sweep (CSR positions) and of the edge sweep (edge ids)
+    const int qA0 = tid * la, nA = max(0, min(la, 2 * m - qA0));
+    const int eE0 = tid * le, nE = max(0, min(le, m - eE0));
+    const uint2 thrA = P.thrA[tid];
+    const int iE0 = P.thrE[tid];
     const int par = st->par;
     const R beta = (R)st->beta;
     const R onepb = (R)(1.0 + st->beta);
@@ -164,7 +169,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     float* __restrict__ Alo_out = P.Alo[par ^ 1];
     const R* __restrict__ D1g = P.Dl[par];       // Delta_{m-1}
     R* __restrict__ D0g = P.Dl[par ^ 1];         // Delta_m (written)
-    const Vec<R, 2>* __restrict__ tq = reinterpret_cast<const Vec<R, 2>*>(P.t[par]);  // (t_m, t_{m-1}) per entry
+    const Vec<R, 2>* __restrict__ tA = reinterpret_cast<const Vec<R, 2>*>(P.t[par]);  // (t_m, t_{m-1})
+    const Vec<R, 2>* __restrict__ tE = tA + LA;
     const R* __restrict__ Xg = P.X;
     const uint32_t* __restrict__ maskg = P.mask;
 
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         bX[b] = reinterpret_cast<V*>(sp);
         sp += sizeof(V) * (size_t)n;
         bM[b] = reinterpret_cast<uint32_t*>(sp);
-        sp += 16 * (size_t)n;
+        sp += SliceLayout<R>::mask_bytes(n);
     }
     if (!PREF) {
         bAhi[1] = bAhi[0];
@@ -197,18 +203,16 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     V* sD0 = reinterpret_cast<V*>(sp);
     sp += sizeof(V) * (size_t)n;
     V* sPart = reinterpret_cast<V*>(sp);
-    sp += sizeof(V) * (size_t)nch;
-    uint4* sEch = reinterpret_cast<uint4*>(sp);
-    sp += sizeof(uint4) * (size_t)ech;
-    uint2* sNch = reinterpret_cast<uint2*>(sp);
-    sp += sizeof(uint2) * (size_t)nch;
+    sp += sizeof(V) * (size_t)P.nslots;
     int* sRow = reinterpret_cast<int*>(sp);
-    int* sNc0 = sRow + n + 1;
-    sp += sizeof(int) * 2 * (size_t)(n + 1);
+    int* sErow = sRow + n + 1;
+    int* sPs0 = sErow + n + 1;
+    sp += sizeof(int) * 3 * (size_t)(n + 1);
     sp = smem_raw + ((size_t)(sp - smem_raw) + 15) / 16 * 16;
     float* sNb = reinterpret_cast<float*>(sp);
-    sp += sizeof(float) * (size_t)m;
-    uint16_t* sCsr = reinterpret_cast<uint16_t*>(sp);
+    sp += sizeof(float) * (size_t)LE;
+    uint16_t* sCsrT = reinterpret_cast<uint16_t*>(sp);
+    uint16_t* sEjT = sCsrT + LA;
     __shared__ double red[32];
 
     auto stage = [&](int sl, int b) {
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
             copy_vec_async(&dD[i], reinterpret_cast<const V*>(D1g + off));
             copy_vec_async(&dX[i], reinterpret_cast<const V*>(Xg + off));
             if constexpr (FF) copy_vec_async(&dL[i], reinterpret_cast<const VF*>(Alo_in + off));
-            if (maskg) cp_async4(&dM[4 * i], maskg + (size_t)i * P.ldw + (c0 >> 5));
+            if (maskg) cp_async4(&dM[i], maskg + (size_t)i * P.ldw + (c0 >> 5));
         }
         cp_async_commit();
     };
@@ -234,12 +238,14 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     // launch-constant graph data
     for (int k = tid; k <= n; k += kSliceThreads) {
         sRow[k] = P.rowptr[k];
-        sNc0[k] = P.nc0[k];
+        sErow[k] = P.erow[k];
+        sPs0[k] = P.ps0[k];
     }
-    for (int k = tid; k < 2 * m; k += kSliceThreads) sCsr[k] = P.csr[k];
-    for (int k = tid; k < nch; k += kSliceThreads) sNch[k] = P.nchunk[k];
-    for (int k = tid; k < ech; k += kSliceThreads) sEch[k] = P.echunk[k];
-    for (int e = tid; e < m; e += kSliceThreads) sNb[e] = 0.f;
+    for (int k = tid; k < LA; k += kSliceThreads) sCsrT[k] = P.csrT[k];
+    for (int k = tid; k < LE; k += kSliceThreads) {
+        sEjT[k] = P.ejT[k];
+        sNb[k] = 0.f;
+    }
     double s_ua = 0.0, s_vb = 0.0, s_rs = 0.0, s_st = 0.0, s_na = 0.0, s_nz = 0.0, s_dl = 0.0;
 
     for (int sl = blockIdx.x; sl < P.nslices; sl += G) {
@@ -255,27 +261,43 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         const uint32_t* __restrict__ sM = cur ? bM[1] : bM[0];
         float f_ua = 0.f, f_vb = 0.f, f_rs = 0.f, f_st = 0.f, f_na = 0.f, f_nz = 0.f, f_dl = 0.f;
 
-        // ---- node phase A: work items of <= kChunk neighbours (hubs of the kNN graph
-        //      have ~15x the median degree; splitting keeps the warps balanced)
-        for (int k = tid; k < nch; k += kSliceThreads) {
-            const uint2 ch = sNch[k];
-            const int i = (int)(ch.y & 0xFFFFu), len = (int)(ch.y >> 16);
-            const int r0 = (int)ch.x, r1 = r0 + len;
-            const V a = sAhi[i];
-            const V d1 = sD1[i];
+        // ---- node sweep: G_i = sum over neighbours of the extrapolated D^T V_y terms.
+        //      Each thread walks its run of CSR entries in order; a partial sum is
+        //      written whenever the run leaves a row (and at its end).
+        if (nA > 0) {
+            int i = (int)thrA.x, slot = (int)thrA.y, rend = sRow[i + 1];
+            V a = sAhi[i];
+            V d1 = sD1[i];
             VF al;
             if constexpr (FF) al = sAlo[i];
             R G_[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) G_[c] = (R)0;
-            // (t_m, t_{m-1}) are stored per CSR entry: a sequential read, two kept in flight
-            Vec<R, 2> tq0 = tq[r0], tq1;
-            if (r0 + 1 < r1) tq1 = tq[r0 + 1];
-            for (int q = r0; q < r1; ++q) {
-                const Vec<R, 2> t2 = tq0;
-                tq0 = tq1;
-                if (q + 2 < r1) tq1 = tq[q + 2];
-                const int j = sCsr[q];
+            Vec<R, 2> tn0 = tA[tid], tn1;
+            if (nA > 1) tn1 = tA[T + tid];
+            int jn = sCsrT[tid];
+            for (int k = 0; k < nA; ++k) {
+                const Vec<R, 2> t2 = tn0;
+                tn0 = tn1;
+                if (k + 2 < nA) tn1 = tA[(k + 2) * T + tid];
+                const int j = jn;
+                if (k + 1 < nA) jn = sCsrT[(k + 1) * T + tid];
+                if (qA0 + k == rend) {
+                    V gp;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        gp.v[c] = G_[c];
+                        G_[c] = (R)0;
+                    }
+                    sPart[slot++] = gp;
+                    do {
+                        ++i;
+                        rend = sRow[i + 1];
+                    } while (rend <= qA0 + k);
+                    a = sAhi[i];
+                    d1 = sD1[i];
+                    if constexpr (FF) al = sAlo[i];
+                }
                 const R ca = onepb * t2.v[0];
                 const R cb = beta * t2.v[1];
                 const V bj = sAhi[j];
@@ -293,7 +315,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
             V gp;
 #pragma unroll
             for (int c = 0; c < C; ++c) gp.v[c] = G_[c];
-            sPart[k] = gp;
+            sPart[slot] = gp;
         }
         __syncthreads();
 
@@ -302,11 +324,11 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         V qv0, qv1, ev0, ev1;
         if (maskg) {
             const int i0 = tid, i1 = tid + kSliceThreads;
-            if (i0 < n && ((sM[4 * i0] >> (c0 & 31)) & 0xFu) != 0xFu) {
+            if (i0 < n && ((sM[i0] >> (c0 & 31)) & 0xFu) != 0xFu) {
                 qv0 = *reinterpret_cast<const V*>(P.Q + (size_t)i0 * ld + c0);
                 ev0 = *reinterpret_cast<const V*>(P.Em + (size_t)i0 * ld + c0);
             }
-            if (i1 < n && ((sM[4 * i1] >> (c0 & 31)) & 0xFu) != 0xFu) {
+            if (i1 < n && ((sM[i1] >> (c0 & 31)) & 0xFu) != 0xFu) {
                 qv1 = *reinterpret_cast<const V*>(P.Q + (size_t)i1 * ld + c0);
                 ev1 = *reinterpret_cast<const V*>(P.Em + (size_t)i1 * ld + c0);
             }
@@ -314,7 +336,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         for (int i = tid, u = 0; i < n; i += kSliceThreads, ++u) {
             const size_t off = (size_t)i * ld + c0;
             const V x = sX[i];
-            const uint32_t obs = maskg ? (sM[4 * i] >> (c0 & 31)) & 0xFu : 0xFu;
+            const uint32_t obs = maskg ? (sM[i] >> (c0 & 31)) & 0xFu : 0xFu;
             V qv, ev;
             if (obs != 0xFu) {
                 if (u == 0) {
@@ -335,7 +357,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
             R G_[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) G_[c] = (R)0;
-            for (int k = sNc0[i]; k < sNc0[i + 1]; ++k) {     // fixed order: deterministic
+            for (int k = sPs0[i]; k < sPs0[i + 1]; ++k) {     // fixed order: deterministic
                 const V gp = sPart[k];
 #pragma unroll
                 for (int c = 0; c < C; ++c) G_[c] += gp.v[c];
@@ -400,24 +422,35 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         }
         __syncthreads();
 
-        // ---- edge phase, over work items of <= kChunk edges (i, j > i):
-        //      b_m = b_{m-1} + (Delta_m,i - Delta_m,j); ||b_m||^2 and ||V_y - B_m||^2
-        for (int k = tid; k < ech; k += kSliceThreads) {
-            const uint4 ch = sEch[k];
-            const int i = (int)(ch.y & 0xFFFFu), len = (int)(ch.y >> 16);
-            const int r0 = (int)ch.x, r1 = r0 + len, e0 = (int)ch.z - r0;
-            const V a = sAhi[i];
-            const V d1 = sD1[i];
-            const V d0 = sD0[i];
+        // ---- edge sweep: b_m = b_{m-1} + (Delta_m,i - Delta_m,j); ||b_m||^2 per edge
+        //      and ||V_y - B_m||^2.  Each thread walks its run of edges (sorted by
+        //      (i, j)), reloading the smaller endpoint's rows when i changes.
+        if (nE > 0) {
+            int i = iE0, rend = sErow[i + 1];
+            V a = sAhi[i];
+            V d1 = sD1[i];
+            V d0 = sD0[i];
             VF al;
             if constexpr (FF) al = sAlo[i];
-            Vec<R, 2> tq0 = tq[r0], tq1;
-            if (r0 + 1 < r1) tq1 = tq[r0 + 1];
-            for (int q = r0; q < r1; ++q) {
-                const Vec<R, 2> t2 = tq0;
-                tq0 = tq1;
-                if (q + 2 < r1) tq1 = tq[q + 2];
-                const int j = sCsr[q], e = e0 + q;        // edges are numbered in (i, j) order
+            Vec<R, 2> tn0 = tE[tid], tn1;
+            if (nE > 1) tn1 = tE[T + tid];
+            int jn = sEjT[tid];
+            for (int k = 0; k < nE; ++k) {
+                const Vec<R, 2> t2 = tn0;
+                tn0 = tn1;
+                if (k + 2 < nE) tn1 = tE[(k + 2) * T + tid];
+                const int j = jn;
+                if (k + 1 < nE) jn = sEjT[(k + 1) * T + tid];
+                if (eE0 + k == rend) {
+                    do {
+                        ++i;
+                        rend = sErow[i + 1];
+                    } while (rend <= eE0 + k);
+                    a = sAhi[i];
+                    d1 = sD1[i];
+                    d0 = sD0[i];
+                    if constexpr (FF) al = sAlo[i];
+                }
                 const R ta = onepb * t2.v[0];
                 const R tb = beta * t2.v[1];
                 const V bj = sAhi[j];
@@ -439,7 +472,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
                     sb += b * b;
                     sv += vmb * vmb;
                 }
-                sNb[e] += (float)sb;     // edge e lies in exactly one work item
+                sNb[k * T + tid] += (float)sb;   // position owned by this thread
                 f_vb += (float)sv;
             }
         }
@@ -455,7 +488,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     }
 
     // ---- partials of this CTA
-    for (int e = tid; e < m; e += kSliceThreads) P.Pnb[(size_t)blockIdx.x * m + e] = sNb[e];
+    for (int k = tid; k < LE; k += kSliceThreads) P.Pnb[(size_t)blockIdx.x * LE + k] = sNb[k];
     double* ps = P.Ps + (size_t)blockIdx.x * kNumScalarPartials;
     double r;
     r = block_sum(s_ua, red);
@@ -496,34 +529,44 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
         acc = warp_sum(acc);
         if (tid == 0) s_d = sqrt(acc + st->eps);
     }
+    // one lane per edge-sweep position pos = k*T + t, the k-th edge of run t
+    const int LA = P.la * kSliceThreads, LE = P.le * kSliceThreads;
     const int lane = tid % kRedEdges, grp = tid / kRedEdges;
-    const int e = blockIdx.x * kRedEdges + lane;
+    const int pos = blockIdx.x * kRedEdges + lane;
+    int e = -1;
+    if (pos < LE) {
+        const int k = pos / kSliceThreads, t = pos - k * kSliceThreads;
+        if (t * P.le + k < m) e = t * P.le + k;
+    }
     double s = 0.0;
-    if (e < m)
-        for (int g = grp; g < G; g += kRedGroups) s += (double)P.Pnb[(size_t)g * m + e];
+    if (e >= 0)
+        for (int g = grp; g < G; g += kRedGroups) s += (double)P.Pnb[(size_t)g * LE + pos];
     part[grp][lane] = s;
     __syncthreads();
     const double d = s_d;
     if (grp == 0) {
         const double gamma = st->gamma, rho = st->rho;
-        const R* tin = P.t[st->par];
-        R* tout = P.t[st->par ^ 1];          // (t_{m+1}, t_m) replaces (t_m, t_{m-1})
+        const R* tEin = P.t[st->par] + 2 * (size_t)LA;
+        R* tAout = P.t[st->par ^ 1];          // (t_{m+1}, t_m) replaces (t_m, t_{m-1})
+        R* tEout = tAout + 2 * (size_t)LA;
         bool fz = false;
         unsigned long long h = 0ULL;
-        if (e < m) {
+        if (e >= 0) {
             double tot = 0.0;
             for (int g = 0; g < kRedGroups; ++g) tot += part[g][lane];
             const double nb = sqrt(tot);
             const double lhs = gamma * P.w[e] * d;
             const double rhs = rho * nb;
             fz = lhs >= rhs;                 // the prox returns exactly zero
-            const int qa = P.qpos[2 * e], qb = P.qpos[2 * e + 1];
             const R tnew = fz ? (R)1 : (R)(lhs / rhs);
-            const R told = tin[2 * qa];
-            tout[2 * qa] = tnew;
-            tout[2 * qa + 1] = told;
-            tout[2 * qb] = tnew;
-            tout[2 * qb + 1] = told;
+            const R told = tEin[2 * pos];
+            tEout[2 * pos] = tnew;
+            tEout[2 * pos + 1] = told;
+            const int2 qp = P.posA[pos];       // the edge's two node-sweep positions
+            tAout[2 * qp.x] = tnew;
+            tAout[2 * qp.x + 1] = told;
+            tAout[2 * qp.y] = tnew;
+            tAout[2 * qp.y + 1] = told;
             P.nb[e] = nb;
             P.fused[e] = fz ? 1 : 0;
             if (fz) h = mix64((unsigned long long)e + 1ULL);
@@ -664,11 +707,10 @@ __global__ void pd_init_kernel(IterParams<R> P, const R* Y0, size_t total) {
             P.Em[k] = (R)0;
         }
     }
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * (size_t)P.m; q += (size_t)gridDim.x * blockDim.x) {
-        P.t[0][2 * q] = (R)1;   // t = 1 - s with s = 0: V_0 = 0 (and V_{-1} = 0)
-        P.t[0][2 * q + 1] = (R)1;
-        P.t[1][2 * q] = (R)1;
-        P.t[1][2 * q + 1] = (R)1;
+    const size_t npairs = ((size_t)P.la + P.le) * kSliceThreads;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * npairs; q += (size_t)gridDim.x * blockDim.x) {
+        P.t[0][q] = (R)1;   // t = 1 - s with s = 0: V_0 = 0 (and V_{-1} = 0)
+        P.t[1][q] = (R)1;
     }
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)P.m; e += (size_t)gridDim.x * blockDim.x) {
         P.nb[e] = 0.0;
@@ -762,14 +804,14 @@ cudaError_t launch_slice(const IterParams<R>& P, size_t smem, cudaStream_t s) {
 
 }  // namespace
 
-size_t pd_slice_smem_bytes(int n, int m, int nch, int ech, bool fp64, bool prefetch) {
-    return fp64 ? SliceLayout<double>::bytes(n, m, nch, ech, prefetch)
-                : SliceLayout<float>::bytes(n, m, nch, ech, prefetch);
+size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch) {
+    return fp64 ? SliceLayout<double>::bytes(n, la, le, nslots, prefetch)
+                : SliceLayout<float>::bytes(n, la, le, nslots, prefetch);
 }
 
 constexpr size_t kPrefetchSmemMax = 160 * 1024;
 
-int pd_reduce_blocks(int m) { return m > 0 ? (m + kRedEdges - 1) / kRedEdges : 1; }
+int pd_reduce_blocks(int le) { return (le * kSliceThreads + kRedEdges - 1) / kRedEdges; }
 
 // largest dynamic shared memory a block may use on this device (static part excluded)
 static size_t slice_smem_limit() {
@@ -789,16 +831,16 @@ cudaError_t launch_pd_slice(const IterParams<R>& P, cudaStream_t s) {
     count_launches(1);
     // the double buffer is worth it only while at least ~96 KB of the SM's
     // 256 KB L1/shared array stays L1 for the per-edge weights and row loads
-    const size_t with_pref = pd_slice_smem_bytes(P.n, P.m, P.nch, P.ech, fp64, true);
+    const size_t with_pref = pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, true);
     if (with_pref <= slice_smem_limit() && with_pref <= kPrefetchSmemMax)
         return launch_slice<R, true>(P, with_pref, s);
-    return launch_slice<R, false>(P, pd_slice_smem_bytes(P.n, P.m, P.nch, P.ech, fp64, false), s);
+    return launch_slice<R, false>(P, pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false), s);
 }
 
 template <typename R>
 cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s) {
     count_launches(1);
-    pd_reduce_kernel<R><<<pd_reduce_blocks(P.m), kReduceThreads, 0, s>>>(P);
+    pd_reduce_kernel<R><<<pd_reduce_blocks(P.le), kReduceThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 
