@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -107,6 +108,7 @@ struct ccx_problem {
     uint2* d_thrA = nullptr;
     int* d_thrE = nullptr;
     int2* d_posA = nullptr;
+    int* d_eid = nullptr;
     int la = 1, le = 1, nslots = 0;
     // path state
     void* A[2] = {nullptr, nullptr};
@@ -186,6 +188,8 @@ void free_edges(ccx_problem* pr) {
     cudaFree(pr->d_thrA);
     cudaFree(pr->d_thrE);
     cudaFree(pr->d_posA);
+    cudaFree(pr->d_eid);
+    pr->d_eid = nullptr;
     pr->d_ei = pr->d_ej = pr->d_rowptr = pr->d_erow = pr->d_ps0 = pr->d_thrE = nullptr;
     pr->d_csrT = pr->d_ejT = nullptr;
     pr->d_thrA = nullptr;
@@ -224,6 +228,88 @@ ccx_status leave(ccx_problem* pr) {
     CUDA_TRY(cudaStreamWaitEvent(pr->user, pr->ev_done, 0));
     CUDA_TRY(cudaStreamSynchronize(pr->work));
     return CCX_OK;
+}
+
+// Order of the entries inside the runs of one sweep.  A sweep's N entries
+// (0..N-1) are cut into T runs of L consecutive entries; entry x gathers the
+// shared-memory row of node val[x] and belongs to segment seg[x] (its row).
+// Within a run the entries of one segment may be taken in any order.  128-bit
+// shared loads are served eight lanes at a time, and lanes whose rows fall in
+// the same 16-byte bank group (node mod ncol) are served one after another, so
+// at every step the eight runs of each group of lanes are given rows in
+// distinct bank groups where their segments allow it (a bipartite matching of
+// lanes to bank groups per step).  Returns at[k*T + t] = entry taken by run t at
+// step k (-1 past the end).
+std::vector<int64_t> arrange_runs(int T, int L, int64_t N, const std::vector<int>& val, const std::vector<int>& seg,
+                                  int ncol) {
+    std::vector<int64_t> at((size_t)L * T, -1);
+    for (int g = 0; g < T; g += 8) {
+        const int nl = std::min(8, T - g);
+        std::vector<int64_t> next(nl), end(nl);     // next unstarted entry, end of the run
+        std::vector<std::vector<int64_t>> rem(nl);  // remaining entries of the current segment
+        for (int l = 0; l < nl; ++l) {
+            next[l] = std::min<int64_t>((int64_t)(g + l) * L, N);
+            end[l] = std::min<int64_t>(next[l] + L, N);
+        }
+        auto refill = [&](int l) {
+            if (!rem[l].empty() || next[l] >= end[l]) return;
+            const int64_t a = next[l];
+            int64_t b = a;
+            while (b < end[l] && seg[b] == seg[a]) ++b;
+            for (int64_t x = a; x < b; ++x) rem[l].push_back(x);
+            next[l] = b;
+        };
+        for (int k = 0; k < L; ++k) {
+            std::vector<int> lanes;
+            std::vector<std::vector<int>> cnt(nl, std::vector<int>(ncol, 0));
+            for (int l = 0; l < nl; ++l) {
+                refill(l);
+                if (rem[l].empty()) continue;
+                lanes.push_back(l);
+                for (int64_t x : rem[l]) cnt[l][val[x] % ncol]++;
+            }
+            auto nopt = [&](int l) {
+                int c = 0;
+                for (int q = 0; q < ncol; ++q) c += cnt[l][q] > 0;
+                return c;
+            };
+            std::stable_sort(lanes.begin(), lanes.end(), [&](int a, int b) { return nopt(a) < nopt(b); });
+            std::vector<int> owner(ncol, -1), lane_col(nl, -1);
+            std::function<bool(int, std::vector<char>&)> augment = [&](int l, std::vector<char>& seen) {
+                std::vector<int> cols;
+                for (int q = 0; q < ncol; ++q)
+                    if (cnt[l][q] > 0) cols.push_back(q);
+                std::stable_sort(cols.begin(), cols.end(), [&](int a, int b) { return cnt[l][a] > cnt[l][b]; });
+                for (int q : cols) {
+                    if (seen[q]) continue;
+                    seen[q] = 1;
+                    if (owner[q] < 0 || augment(owner[q], seen)) {
+                        owner[q] = l;
+                        lane_col[l] = q;
+                        return true;
+                    }
+                }
+                return false;
+            };
+            for (int l : lanes) {
+                std::vector<char> seen(ncol, 0);
+                augment(l, seen);
+            }
+            for (int l : lanes) {
+                int q = lane_col[l];
+                if (q < 0 || owner[q] != l) {   // unmatched: take the most common bank group
+                    q = 0;
+                    for (int c = 1; c < ncol; ++c)
+                        if (cnt[l][c] > cnt[l][q]) q = c;
+                }
+                size_t pick = 0;
+                while (val[rem[l][pick]] % ncol != q) ++pick;
+                at[(size_t)k * T + g + l] = rem[l][pick];
+                rem[l].erase(rem[l].begin() + (long)pick);
+            }
+        }
+    }
+    return at;
 }
 
 // Validate, sort by (i, j), drop zero weights, store and upload with CSR.
@@ -291,10 +377,27 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
     const int64_t m2 = 2 * (int64_t)m;
     const int la = (int)std::max<int64_t>(1, (m2 + T - 1) / T);
     const int le = std::max(1, (m + T - 1) / T);
-    auto posA = [&](int64_t q) { return (int)((q % la) * T + q / la); };
+    // bank groups of a node's 16-byte shared rows: 8 for float rows (16 bytes), 4 for double rows
+    const int ncol = pr->precision == CCX_FP64 ? 4 : 8;
+    std::vector<int> csr_val(csr.begin(), csr.end());
+    const std::vector<int64_t> atA = arrange_runs(T, la, m2, csr_val, rowof, ncol);
+    const std::vector<int64_t> atE = arrange_runs(T, le, m, pr->ej, pr->ei, ncol);
+    std::vector<int> posA_of(m2 > 0 ? m2 : 1);
     std::vector<uint16_t> csrT((size_t)la * T, 0), ejT((size_t)le * T, 0);
-    for (int64_t q = 0; q < m2; ++q) csrT[posA(q)] = csr[q];
-    for (int e = 0; e < m; ++e) ejT[(size_t)(e % le) * T + e / le] = (uint16_t)pr->ej[e];
+    for (size_t x = 0; x < atA.size(); ++x)
+        if (atA[x] >= 0) {
+            csrT[x] = csr[atA[x]];
+            posA_of[atA[x]] = (int)x;
+        }
+    std::vector<int> eid((size_t)le * T, -1);
+    std::vector<int2> posE((size_t)le * T, make_int2(0, 0));
+    for (size_t x = 0; x < atE.size(); ++x)
+        if (atE[x] >= 0) {
+            const int e = (int)atE[x];
+            ejT[x] = (uint16_t)pr->ej[e];
+            eid[x] = e;
+            posE[x] = make_int2(posA_of[qa[e]], posA_of[qb[e]]);
+        }
     // node-sweep partial slots: one per (run, row) overlap, numbered in entry
     // order, so the slots of a node are consecutive
     std::vector<uint2> thrA(T);
@@ -315,8 +418,6 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
     for (int64_t i = 0; i < n; ++i) erow[i + 1] += erow[i];
     for (int t = 0; t < T; ++t)
         if ((int64_t)t * le < m) thrE[t] = pr->ei[(size_t)t * le];
-    std::vector<int2> posE((size_t)le * T, make_int2(0, 0));
-    for (int e = 0; e < m; ++e) posE[(size_t)(e % le) * T + e / le] = make_int2(posA(qa[e]), posA(qb[e]));
     free_path(pr);
     free_edges(pr);
     pr->la = la;
@@ -333,6 +434,7 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
     CUDA_TRY(dalloc(&pr->d_thrA, T));
     CUDA_TRY(dalloc(&pr->d_thrE, T));
     CUDA_TRY(dalloc(&pr->d_posA, posE.size()));
+    CUDA_TRY(dalloc(&pr->d_eid, eid.size()));
     if (m > 0) {
         CUDA_TRY(cudaMemcpy(pr->d_ei, pr->ei.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(pr->d_ej, pr->ej.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
@@ -343,6 +445,7 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
     CUDA_TRY(cudaMemcpy(pr->d_thrA, thrA.data(), sizeof(uint2) * T, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pr->d_thrE, thrE.data(), sizeof(int) * T, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pr->d_posA, posE.data(), sizeof(int2) * posE.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pr->d_eid, eid.data(), sizeof(int) * eid.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pr->d_rowptr, rowptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pr->d_erow, erow.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pr->d_ps0, ps0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
@@ -370,6 +473,7 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.thrA = pr->d_thrA;
     P.thrE = pr->d_thrE;
     P.posA = pr->d_posA;
+    P.eid = pr->d_eid;
     P.la = pr->la;
     P.le = pr->le;
     P.nslots = pr->nslots;

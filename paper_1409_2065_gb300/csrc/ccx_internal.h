@@ -85,9 +85,10 @@ struct IterParams {
     // The two edge sweeps of the iteration kernel are split into equal runs,
     // one per thread: thread t takes node-sweep entries (CSR positions over
     // both directions) [t*la, (t+1)*la) and edge-sweep entries (edge ids in
-    // (i, j) order) [t*le, (t+1)*le).  Per-entry arrays of a sweep store the
-    // k-th entry of thread t at k*T + t (T = kSliceThreads), so a warp's k-th
-    // step reads consecutive words.
+    // (i, j) order) [t*le, (t+1)*le), the entries of each row of a run in an
+    // order chosen against shared-memory bank conflicts.  Per-entry arrays of
+    // a sweep store the k-th entry of thread t at k*T + t (T = kSliceThreads),
+    // so a warp's k-th step reads consecutive words.
     R* t[2];                    // (t_m, t_{m-1}) pairs, t = 1 - s: la*T pairs in node-sweep
                                 // order, then le*T pairs in edge-sweep order
     const int* rowptr;          // CSR over both directions, n + 1
@@ -98,6 +99,7 @@ struct IterParams {
     const uint2* thrA;          // T: (node of the first entry, first partial slot) of each node-sweep run
     const int* thrE;            // T: smaller endpoint of the first edge of each edge-sweep run
     const int2* posA;           // le*T: node-sweep positions of the edge at each edge-sweep position
+    const int* eid;             // le*T: edge id at each edge-sweep position (-1: padding)
     const int* ei;              // edge endpoints, i < j
     const int* ej;
     const double* w;            // edge weights

@@ -533,11 +533,7 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     const int LA = P.la * kSliceThreads, LE = P.le * kSliceThreads;
     const int lane = tid % kRedEdges, grp = tid / kRedEdges;
     const int pos = blockIdx.x * kRedEdges + lane;
-    int e = -1;
-    if (pos < LE) {
-        const int k = pos / kSliceThreads, t = pos - k * kSliceThreads;
-        if (t * P.le + k < m) e = t * P.le + k;
-    }
+    const int e = pos < LE ? P.eid[pos] : -1;
     double s = 0.0;
     if (e >= 0)
         for (int g = grp; g < G; g += kRedGroups) s += (double)P.Pnb[(size_t)g * LE + pos];
