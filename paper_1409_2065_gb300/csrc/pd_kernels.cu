@@ -246,7 +246,15 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         sEjT[k] = P.ejT[k];
         sNb[k] = 0.f;
     }
-    double s_ua = 0.0, s_vb = 0.0, s_rs = 0.0, s_st = 0.0, s_na = 0.0, s_nz = 0.0, s_dl = 0.0;
+    // scalar partial sums: per warp, in double, accumulated slice by slice in a fixed order
+    __shared__ double sAcc[kSliceThreads / 32][kNumScalarPartials];
+    for (int k = tid; k < (kSliceThreads / 32) * kNumScalarPartials; k += kSliceThreads) (&sAcc[0][0])[k] = 0.0;
+    const int warp = tid >> 5, lane = tid & 31;
+    auto flush = [&](float v, int slot) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sAcc[warp][slot] += (double)v;
+    };
 
     for (int sl = blockIdx.x; sl < P.nslices; sl += G) {
         const int c0 = sl * C;
@@ -259,7 +267,6 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         const V* __restrict__ sD1 = cur ? bD1[1] : bD1[0];
         const V* __restrict__ sX = cur ? bX[1] : bX[0];
         const uint32_t* __restrict__ sM = cur ? bM[1] : bM[0];
-        float f_ua = 0.f, f_vb = 0.f, f_rs = 0.f, f_st = 0.f, f_na = 0.f, f_nz = 0.f, f_dl = 0.f;
 
         // ---- node sweep: G_i = sum over neighbours of the extrapolated D^T V_y terms.
         //      Each thread walks its run of CSR entries in order; a partial sum is
@@ -275,13 +282,18 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
             for (int c = 0; c < C; ++c) G_[c] = (R)0;
             Vec<R, 2> tn0 = tA[tid], tn1;
             if (nA > 1) tn1 = tA[T + tid];
+            // the neighbour rows of entry k + 1 are requested while entry k is summed
             int jn = sCsrT[tid];
+#pragma unroll 2
             for (int k = 0; k < nA; ++k) {
                 const Vec<R, 2> t2 = tn0;
                 tn0 = tn1;
                 if (k + 2 < nA) tn1 = tA[(k + 2) * T + tid];
-                const int j = jn;
+                const int jc = jn;
                 if (k + 1 < nA) jn = sCsrT[(k + 1) * T + tid];
+                const V cbj = sAhi[jc], cdj = sD1[jc];
+                VF clj;
+                if constexpr (FF) clj = sAlo[jc];
                 if (qA0 + k == rend) {
                     V gp;
 #pragma unroll
@@ -298,18 +310,15 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
                     d1 = sD1[i];
                     if constexpr (FF) al = sAlo[i];
                 }
-                const R ca = onepb * t2.v[0];
+                // (1+beta) t_m b1 - beta t_{m-1} b2 with b2 = b1 - (d1_i - d1_j)
                 const R cb = beta * t2.v[1];
-                const V bj = sAhi[j];
-                const V dj = sD1[j];
-                VF lj;
-                if constexpr (FF) lj = sAlo[j];
+                const R cd = onepb * t2.v[0] - cb;
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    R b1 = a.v[c] - bj.v[c];
-                    if constexpr (FF) b1 += al.v[c] - lj.v[c];
-                    const R b2 = b1 - (d1.v[c] - dj.v[c]);
-                    G_[c] += ca * b1 - cb * b2;
+                    R b1 = a.v[c] - cbj.v[c];
+                    if constexpr (FF) b1 += al.v[c] - clj.v[c];
+                    G_[c] = fma(cd, b1, G_[c]);
+                    G_[c] = fma(cb, d1.v[c] - cdj.v[c], G_[c]);
                 }
             }
             V gp;
@@ -320,6 +329,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         __syncthreads();
 
         // ---- node phase B: one preconditioned correction of the projection per (i, slice)
+        float f_ua = 0.f, f_rs = 0.f, f_st = 0.f, f_na = 0.f, f_nz = 0.f, f_dl = 0.f;
         // missing entries of this thread's first two nodes: issue their loads together
         V qv0, qv1, ev0, ev1;
         if (maskg) {
@@ -422,9 +432,17 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         }
         __syncthreads();
 
+        flush(f_ua, kPsUA);
+        flush(f_rs, kPsRestart);
+        flush(f_st, kPsStep);
+        flush(f_na, kPsNormA);
+        flush(f_nz, kPsNoise);
+        flush(f_dl, kPsDelta);
+
         // ---- edge sweep: b_m = b_{m-1} + (Delta_m,i - Delta_m,j); ||b_m||^2 per edge
         //      and ||V_y - B_m||^2.  Each thread walks its run of edges (sorted by
         //      (i, j)), reloading the smaller endpoint's rows when i changes.
+        float f_vb = 0.f;
         if (nE > 0) {
             int i = iE0, rend = sErow[i + 1];
             V a = sAhi[i];
@@ -435,12 +453,16 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
             Vec<R, 2> tn0 = tE[tid], tn1;
             if (nE > 1) tn1 = tE[T + tid];
             int jn = sEjT[tid];
+#pragma unroll 2
             for (int k = 0; k < nE; ++k) {
                 const Vec<R, 2> t2 = tn0;
                 tn0 = tn1;
                 if (k + 2 < nE) tn1 = tE[(k + 2) * T + tid];
-                const int j = jn;
+                const int jc = jn;
                 if (k + 1 < nE) jn = sEjT[(k + 1) * T + tid];
+                const V cbj = sAhi[jc], cd1j = sD1[jc], cd0j = sD0[jc];
+                VF clj;
+                if constexpr (FF) clj = sAlo[jc];
                 if (eE0 + k == rend) {
                     do {
                         ++i;
@@ -451,38 +473,28 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
                     d0 = sD0[i];
                     if constexpr (FF) al = sAlo[i];
                 }
-                const R ta = onepb * t2.v[0];
+                // V_y - B_m = -(dmv - beta d1v) - ((1+beta) t_m b1 - beta t_{m-1} b2),
+                // b2 = b1 - d1v:  = -dmv + (beta - tb) d1v - (ta - tb) b1
                 const R tb = beta * t2.v[1];
-                const V bj = sAhi[j];
-                const V d1j = sD1[j];
-                const V d0j = sD0[j];
-                VF lj;
-                if constexpr (FF) lj = sAlo[j];
+                const R q1 = beta - tb;
+                const R q2 = tb - onepb * t2.v[0];
                 R sb = (R)0, sv = (R)0;
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
-                    R b1 = a.v[c] - bj.v[c];
-                    if constexpr (FF) b1 += al.v[c] - lj.v[c];
-                    const R d1v = d1.v[c] - d1j.v[c];
-                    const R dmv = d0.v[c] - d0j.v[c];
+                    R b1 = a.v[c] - cbj.v[c];
+                    if constexpr (FF) b1 += al.v[c] - clj.v[c];
+                    const R d1v = d1.v[c] - cd1j.v[c];
+                    const R dmv = d0.v[c] - cd0j.v[c];
                     const R b = b1 + dmv;                   // b_m
-                    const R b2 = b1 - d1v;                  // b_{m-2}
-                    const R Dd = dmv - beta * d1v;          // delta_i - delta_j
-                    const R vmb = -Dd - (ta * b1 - tb * b2);
-                    sb += b * b;
-                    sv += vmb * vmb;
+                    const R vmb = fma(q2, b1, fma(q1, d1v, -dmv));
+                    sb = fma(b, b, sb);
+                    sv = fma(vmb, vmb, sv);
                 }
                 sNb[k * T + tid] += (float)sb;   // position owned by this thread
                 f_vb += (float)sv;
             }
         }
-        s_ua += f_ua;
-        s_vb += f_vb;
-        s_rs += f_rs;
-        s_st += f_st;
-        s_na += f_na;
-        s_nz += f_nz;
-        s_dl += f_dl;
+        flush(f_vb, kPsVB);
         __syncthreads();
         cur ^= (PREF ? 1 : 0);
     }
@@ -490,21 +502,11 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     // ---- partials of this CTA
     for (int k = tid; k < LE; k += kSliceThreads) P.Pnb[(size_t)blockIdx.x * LE + k] = sNb[k];
     double* ps = P.Ps + (size_t)blockIdx.x * kNumScalarPartials;
-    double r;
-    r = block_sum(s_ua, red);
-    if (tid == 0) ps[kPsUA] = r;
-    r = block_sum(s_vb, red);
-    if (tid == 0) ps[kPsVB] = r;
-    r = block_sum(s_rs, red);
-    if (tid == 0) ps[kPsRestart] = r;
-    r = block_sum(s_st, red);
-    if (tid == 0) ps[kPsStep] = r;
-    r = block_sum(s_na, red);
-    if (tid == 0) ps[kPsNormA] = r;
-    r = block_sum(s_nz, red);
-    if (tid == 0) ps[kPsNoise] = r;
-    r = block_sum(s_dl, red);
-    if (tid == 0) ps[kPsDelta] = r;
+    if (tid < kNumScalarPartials) {
+        double r = 0.0;
+        for (int w = 0; w < kSliceThreads / 32; ++w) r += sAcc[w][tid];
+        ps[tid] = r;
+    }
 }
 
 // ------------------------------------------------------------------ reduce
