@@ -90,8 +90,10 @@ typedef struct {
 /* Per-gamma statistics. */
 typedef struct {
     int iters;         /* MM iterations spent on this gamma */
-    int converged;     /* 1: error estimate <= tol; 2: stopped because the iterate only moves at the
-                          rounding level (no 10 % progress for a long stretch); 0: max_iter reached */
+    int converged;     /* 1: error estimate <= tol; 2: stopped at the rounding level of the arithmetic
+                          (steps at the level of their own rounding noise, or a residual that no longer
+                          falls while the estimate from its last measured decay rate is <= 100 tol);
+                          0: max_iter reached */
     int n_fused;       /* fused edges at the returned iterate */
     int n_clusters;    /* connected components of the fused edges */
     double gamma, rho, eps;

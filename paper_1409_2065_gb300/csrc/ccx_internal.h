@@ -30,6 +30,9 @@ constexpr int kNumScalarPartials = 8;
 constexpr double kStallSteps = 128.0;  // error bound, in steps, once steps are at the rounding level
 constexpr double kNoiseFactor = 8.0;   // steps within this factor of the rounding noise: no progress possible
 constexpr int kNoiseWindows = 8;       // consecutive such windows before stopping
+constexpr int kStallWindows = 16;      // windows without a 2x residual decrease over kRateWindows before a plateau exit
+constexpr double kStallTolFactor = 100.0;  // a plateau exit needs the rate-based error estimate within this x tol
+constexpr double kFuseMargin = 1e-5;   // relative margin of a "clearly fused" edge (mu w d >= rho ||b|| (1 + margin))
 
 // Scalar partial slots written by each CTA of the iteration kernel.
 enum : int {
@@ -56,9 +59,11 @@ struct PdState {
     double noise_max;     // window maximum of the rounding-noise scale of the step
     double dmax;          // window maximum of ||A_m - A_start|| (the map's residual)
     double ring[kRateWindows];  // recent window maxima of that residual
+    double g_last;        // last measured residual decay rate per iteration (0: none yet)
     int ring_len;
     int floor_hits;       // consecutive windows with steps at the rounding level
-    unsigned long long fused_hash;
+    int stall_hits;       // consecutive windows in which the residual made no 2x progress
+    unsigned long long fused_hash;   // order-free hash of the clearly fused edges
     int k_mom;
     int accelerate;
     int par;              // slot parity: input slots of the next iteration

@@ -567,7 +567,10 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
             tAout[2 * qp.y + 1] = told;
             P.nb[e] = nb;
             P.fused[e] = fz ? 1 : 0;
-            if (fz) h = mix64((unsigned long long)e + 1ULL);
+            // the stability test of the stopping rule follows only the clearly
+            // fused edges: an edge on the threshold may flip at rounding level
+            // for ever without the iterate changing
+            if (lhs >= rhs * (1.0 + kFuseMargin)) h = mix64((unsigned long long)e + 1ULL);
         }
         const unsigned ballot = __ballot_sync(0xffffffffu, fz);
 #pragma unroll
@@ -629,7 +632,7 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     } else {
         st->beta = 0.0;
     }
-    if ((int)nf == st->n_fused && hash == st->fused_hash) st->fused_stable += 1;
+    if (hash == st->fused_hash) st->fused_stable += 1;
     else st->fused_stable = 0;
     st->n_fused = (int)nf;
     st->fused_hash = hash;
@@ -652,13 +655,21 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
         // only when the centroids are ~0, e.g. fully fused centred data)
         const double scale = fmax(an, st->scale_floor);
         double est = INFINITY;
+        const bool full = st->ring_len == kRateWindows;
         if (cur == 0.0) {
             est = 0.0;
-        } else if (st->ring_len == kRateWindows && cur < st->ring[0]) {
+        } else if (full && cur < st->ring[0]) {
             const double g = log(st->ring[0] / cur) / (double)(kRateWindows * kConvWindow);
             est = cur / (g * g) / scale;
+            if (cur <= 0.5 * st->ring[0]) st->g_last = g;
         }
         st->err_est = est;
+        // plateau: the residual has stopped falling (rounding level of this
+        // state); its error is the plateau residual over the last measured rate
+        const bool stalled = full && cur > 0.5 * st->ring[0];
+        st->stall_hits = stalled ? st->stall_hits + 1 : 0;
+        double est_plateau = INFINITY;
+        if (st->g_last > 0.0) est_plateau = cur / (st->g_last * st->g_last) / scale;
         if (est <= st->tol && st->fused_stable >= kConvWindow) st->hits += 1;
         else st->hits = 0;
         // steps at the rounding level of their own inputs: no further progress
@@ -672,6 +683,13 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
             st->done = 1;
             st->converged = 2;
             st->err_est = st->blk_max * kStallSteps / scale;
+        } else if (st->stall_hits >= kStallWindows && st->fused_stable >= kStallWindows * kConvWindow &&
+                   est_plateau <= kStallTolFactor * st->tol && cur <= unit * sqrt(unit) * scale) {
+            // (a slowly converging mode also looks flat over a few windows; its
+            // residual is far above u^1.5 of the solution's scale)
+            st->done = 1;
+            st->converged = 2;
+            st->err_est = est_plateau;
         }
         for (int q = 0; q + 1 < kRateWindows; ++q) st->ring[q] = st->ring[q + 1];
         st->ring[kRateWindows - 1] = cur;
@@ -753,6 +771,8 @@ __global__ void pd_begin_gamma_kernel(PdState* st, double gamma, double rho, dou
     st->noise_max = 0.0;
     st->ring_len = 0;
     st->floor_hits = 0;
+    st->stall_hits = 0;
+    st->g_last = 0.0;
     for (int q = 0; q < kRateWindows; ++q) st->ring[q] = 0.0;
     st->dmax = 0.0;
     st->counter = 0u;
