@@ -118,6 +118,21 @@ def test_knn_matches_oracle_missing_normalized(ccx):
     assert abs(w.sum() - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("n,p,k,frac", [(400, 2000, 10, 0.05), (130, 37, 5, 0.0), (257, 300, 9, 0.1)])
+def test_knn_tensor_core_gram_shapes(ccx, n, p, k, frac):
+    """Candidate selection from the tensor-core Gram: tiles with ragged rows (n not a multiple of 128),
+    short and long K, missing data; the edge set must equal brute force exactly."""
+    X, mask, _ = synth.genotype_like(n, p, 5, seed=31, fst=0.05, frac_missing=frac)
+    if frac == 0.0:
+        mask = None
+    pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+    pr.build_knn(k, phi_auto=True, normalize=True)
+    ei, ej, w = pr.get_edges()
+    oei, oej, ow, _, _ = O.knn_gaussian_weights(X.astype(np.float64), mask, k, "auto", True)
+    assert np.array_equal(ei, oei) and np.array_equal(ej, oej)
+    assert np.allclose(w, ow, rtol=1e-12, atol=0)
+
+
 def test_knn_all_pairs(ccx):
     X, _ = synth.expression_like(20, 300, 3, 40, seed=2)
     pr = ccx.Problem(X, None, ccx.CCX_FP32)
