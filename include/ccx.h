@@ -85,6 +85,10 @@ typedef struct {
     int max_iter;      /* MM iterations per gamma; default 200000 */
     int accelerate;    /* 1: Nesterov-extrapolated MM with restarts (default); 0: the plain MM iteration */
     int chunk;         /* iterations per captured CUDA graph launch; default 64 */
+    int stream_edges;  /* 0 (default): the iteration kernel keeps the per-edge index and accumulator
+                          arrays in shared memory when they fit beside the rows of a slice, and in
+                          global memory otherwise; 1: always in global memory.  Results are
+                          identical either way (same arithmetic in the same order). */
 } ccx_opts;
 
 /* Per-gamma statistics. */

@@ -133,6 +133,8 @@ struct ccx_problem {
     bool path_started = false;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
+    int graph_stream = 0;        // stream_edges the captured graph was built with
+    int stream_edges = 0;        // from the options of the current call
 };
 
 namespace {
@@ -477,6 +479,7 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.la = pr->la;
     P.le = pr->le;
     P.nslots = pr->nslots;
+    P.stream_edges = pr->stream_edges;
     P.ei = pr->d_ei;
     P.ej = pr->d_ej;
     P.w = pr->d_w;
@@ -502,11 +505,13 @@ ccx_status check_limits(ccx_problem* pr) {
                                       "(have %lld)", (long long)pr->n);
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pr->device));
-    const size_t need = pd_slice_smem_bytes((int)pr->n, pr->la, pr->le, pr->nslots, pr->precision == CCX_FP64, false);
+    // the smallest variant of the iteration kernel keeps only the rows of a slice in shared memory
+    const size_t need = pd_slice_smem_bytes((int)pr->n, pr->la, pr->le, pr->nslots, pr->precision == CCX_FP64, false,
+                                            true);
     if (need + 2048 > (size_t)optin)
         return fail(CCX_EUNSUPPORTED,
                     "n = %lld cases and %d edges need %zu bytes of shared memory per block (a column slice of "
-                    "all rows plus ~10 bytes per edge); the device allows %d",
+                    "all rows and the partial sums of the node sweep); the device allows %d",
                     (long long)pr->n, m, need, optin);
     return CCX_OK;
 }
@@ -549,7 +554,7 @@ ccx_status ensure_path(ccx_problem* pr) {
 }
 
 ccx_status build_graph(ccx_problem* pr, int chunk) {
-    if (pr->graph && pr->graph_chunk == chunk) return CCX_OK;
+    if (pr->graph && pr->graph_chunk == chunk && pr->graph_stream == pr->stream_edges) return CCX_OK;
     if (pr->graph) {
         cudaGraphExecDestroy(pr->graph);
         pr->graph = nullptr;
@@ -573,6 +578,7 @@ ccx_status build_graph(ccx_problem* pr, int chunk) {
     cudaGraphDestroy(g);
     if (err != cudaSuccess) return fail(CCX_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(err));
     pr->graph_chunk = chunk;
+    pr->graph_stream = pr->stream_edges;
     return CCX_OK;
 }
 
@@ -675,6 +681,7 @@ void ccx_opts_default(ccx_opts* o) {
     o->max_iter = 200000;
     o->accelerate = 1;
     o->chunk = 64;
+    o->stream_edges = 0;
 }
 
 const char* ccx_last_error(void) { return g_err.c_str(); }
@@ -895,6 +902,7 @@ ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, co
     ccx_opts_default(&o);
     if (pr->precision == CCX_FP64) o.tol = 1e-10;
     if (opts) o = *opts;
+    pr->stream_edges = o.stream_edges ? 1 : 0;
     if (!(o.rho_scale > 0.0) || !std::isfinite(o.rho_scale)) return fail(CCX_EINVAL, "rho_scale must be > 0");
     if (!(o.eps_rel > 0.0) || !std::isfinite(o.eps_rel)) return fail(CCX_EINVAL, "eps_rel must be > 0");
     if (!(o.tol > 0.0)) return fail(CCX_EINVAL, "tol must be > 0");
@@ -926,6 +934,7 @@ ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const 
     ccx_opts o;
     ccx_opts_default(&o);
     if (opts) o = *opts;
+    pr->stream_edges = o.stream_edges ? 1 : 0;
     ccx_status s = check_limits(pr);
     if (s != CCX_OK) return s;
     s = enter(pr);

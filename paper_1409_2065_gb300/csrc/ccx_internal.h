@@ -116,6 +116,7 @@ struct IterParams {
     PdState* st;
     int n, ld, ldw, m, nslices, G;
     int la, le, nslots;         // run lengths of the two sweeps; node-sweep partial slots
+    int stream_edges;           // 1: per-entry arrays of the sweeps stay in global memory
 };
 
 // ---------------------------------------------------------------- launchers
@@ -135,7 +136,7 @@ cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s);
 void count_launches(unsigned long long k);
 template <typename R>
 cudaError_t launch_pd_finalize(const IterParams<R>& P, float* U_out, int64_t ld_out, int p, cudaStream_t s);
-size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch);
+size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch, bool stream);
 int pd_reduce_blocks(int le);
 
 // data preparation (prep_kernels.cu)

@@ -130,19 +130,23 @@ struct SliceLayout {
     __host__ __device__ static size_t mask_bytes(int n) { return ((size_t)n * 4 + 15) / 16 * 16; }
     // A_hi (+A_lo) + Delta_{m-1} + X, then the mask words
     static size_t buf(int n) { return (FF ? 4 : 3) * row * (size_t)n + mask_bytes(n); }
-    static size_t bytes(int n, int la, int le, int nslots, bool pref) {
+    // stream: the per-entry arrays (neighbour indices, per-edge accumulators) stay
+    // in global memory, for problems whose edge set does not fit beside the rows
+    static size_t bytes(int n, int la, int le, int nslots, bool pref, bool stream) {
         const size_t LA = (size_t)la * kSliceThreads, LE = (size_t)le * kSliceThreads;
         size_t b = (pref ? 2 : 1) * buf(n) + row * (size_t)n;
         b += row * (size_t)nslots;
         b += sizeof(int) * 3 * (size_t)(n + 1);
         b = (b + 15) / 16 * 16;
-        b += sizeof(float) * LE;
-        b += sizeof(uint16_t) * (LA + LE);
+        if (!stream) {
+            b += sizeof(float) * LE;
+            b += sizeof(uint16_t) * (LA + LE);
+        }
         return (b + 15) / 16 * 16;
     }
 };
 
-template <typename R, bool PREF>
+template <typename R, bool PREF, bool STREAM>
 __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R> P) {
     constexpr bool FF = std::is_same<R, float>::value;
     using V = Vec<R, C>;
@@ -209,10 +213,20 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     int* sPs0 = sErow + n + 1;
     sp += sizeof(int) * 3 * (size_t)(n + 1);
     sp = smem_raw + ((size_t)(sp - smem_raw) + 15) / 16 * 16;
-    float* sNb = reinterpret_cast<float*>(sp);
-    sp += sizeof(float) * (size_t)LE;
-    uint16_t* sCsrT = reinterpret_cast<uint16_t*>(sp);
-    uint16_t* sEjT = sCsrT + LA;
+    float* sNb;                 // per edge-sweep position: this CTA's sum of ||b_m||^2
+    const uint16_t* sCsrT;      // neighbour indices of the two sweeps
+    const uint16_t* sEjT;
+    if constexpr (STREAM) {
+        sNb = P.Pnb + (size_t)blockIdx.x * LE;   // this CTA's own row of the partials
+        sCsrT = P.csrT;
+        sEjT = P.ejT;
+    } else {
+        sNb = reinterpret_cast<float*>(sp);
+        sp += sizeof(float) * (size_t)LE;
+        uint16_t* ci = reinterpret_cast<uint16_t*>(sp);
+        sCsrT = ci;
+        sEjT = ci + LA;
+    }
     __shared__ double red[32];
 
     auto stage = [&](int sl, int b) {
@@ -241,11 +255,13 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         sErow[k] = P.erow[k];
         sPs0[k] = P.ps0[k];
     }
-    for (int k = tid; k < LA; k += kSliceThreads) sCsrT[k] = P.csrT[k];
-    for (int k = tid; k < LE; k += kSliceThreads) {
-        sEjT[k] = P.ejT[k];
-        sNb[k] = 0.f;
+    if constexpr (!STREAM) {
+        uint16_t* ci = const_cast<uint16_t*>(sCsrT);
+        for (int k = tid; k < LA; k += kSliceThreads) ci[k] = P.csrT[k];
+        for (int k = tid; k < LE; k += kSliceThreads) ci[LA + k] = P.ejT[k];
     }
+    // each thread clears the accumulator positions it owns (k * T + tid)
+    for (int k = tid; k < LE; k += kSliceThreads) sNb[k] = 0.f;
     // scalar partial sums: per warp, in double, accumulated slice by slice in a fixed order
     __shared__ double sAcc[kSliceThreads / 32][kNumScalarPartials];
     for (int k = tid; k < (kSliceThreads / 32) * kNumScalarPartials; k += kSliceThreads) (&sAcc[0][0])[k] = 0.0;
@@ -500,7 +516,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
     }
 
     // ---- partials of this CTA
-    for (int k = tid; k < LE; k += kSliceThreads) P.Pnb[(size_t)blockIdx.x * LE + k] = sNb[k];
+    if constexpr (!STREAM)
+        for (int k = tid; k < LE; k += kSliceThreads) P.Pnb[(size_t)blockIdx.x * LE + k] = sNb[k];
     double* ps = P.Ps + (size_t)blockIdx.x * kNumScalarPartials;
     if (tid < kNumScalarPartials) {
         double r = 0.0;
@@ -797,9 +814,9 @@ __global__ void pd_finalize_kernel(IterParams<R> P, float* U_out, int64_t ld_out
     }
 }
 
-template <typename R, bool PREF>
+template <typename R, bool PREF, bool STREAM>
 cudaError_t launch_slice(const IterParams<R>& P, size_t smem, cudaStream_t s) {
-    auto kern = pd_slice_kernel<R, PREF>;
+    auto kern = pd_slice_kernel<R, PREF, STREAM>;
     // The shared-memory opt-in is a function attribute, not a stream
     // operation: it is raised once, to the device maximum, on the first
     // (uncaptured) launch so that launches inside graph capture need no call.
@@ -822,9 +839,9 @@ cudaError_t launch_slice(const IterParams<R>& P, size_t smem, cudaStream_t s) {
 
 }  // namespace
 
-size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch) {
-    return fp64 ? SliceLayout<double>::bytes(n, la, le, nslots, prefetch)
-                : SliceLayout<float>::bytes(n, la, le, nslots, prefetch);
+size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch, bool stream) {
+    return fp64 ? SliceLayout<double>::bytes(n, la, le, nslots, prefetch, stream)
+                : SliceLayout<float>::bytes(n, la, le, nslots, prefetch, stream);
 }
 
 constexpr size_t kPrefetchSmemMax = 160 * 1024;
@@ -849,10 +866,15 @@ cudaError_t launch_pd_slice(const IterParams<R>& P, cudaStream_t s) {
     count_launches(1);
     // the double buffer is worth it only while at least ~96 KB of the SM's
     // 256 KB L1/shared array stays L1 for the per-edge weights and row loads
-    const size_t with_pref = pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, true);
-    if (with_pref <= slice_smem_limit() && with_pref <= kPrefetchSmemMax)
-        return launch_slice<R, true>(P, with_pref, s);
-    return launch_slice<R, false>(P, pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false), s);
+    const size_t lim = slice_smem_limit();
+    if (P.stream_edges)
+        return launch_slice<R, false, true>(P, pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false, true), s);
+    const size_t with_pref = pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, true, false);
+    if (with_pref <= lim && with_pref <= kPrefetchSmemMax) return launch_slice<R, true, false>(P, with_pref, s);
+    const size_t staged = pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false, false);
+    if (staged <= lim) return launch_slice<R, false, false>(P, staged, s);
+    // edge set too large to stage beside the rows: indices and accumulators stay in global memory
+    return launch_slice<R, false, true>(P, pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false, true), s);
 }
 
 template <typename R>

@@ -133,6 +133,44 @@ def test_knn_tensor_core_gram_shapes(ccx, n, p, k, frac):
     assert np.allclose(w, ow, rtol=1e-12, atol=0)
 
 
+def test_streamed_edge_arrays_identical(ccx):
+    """The iteration kernel's variant for large edge sets (indices and per-edge accumulators in
+    global memory) gives bit-identical results to the staged variant."""
+    X, mask, _ = synth.genotype_like(300, 64, 5, seed=41, fst=0.05, frac_missing=0.05)
+    gammas = None
+    out = []
+    for stream in (0, 1):
+        pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+        pr.build_knn(10, phi_auto=True, normalize=True)
+        if gammas is None:
+            g0 = pr.fusion_scale()
+            gammas = synth.log_grid(0.05 * g0, 2.0 * g0, 4)
+        o = ccx.opts_default()
+        o.stream_edges = stream
+        U, labels, stats, st = pr.solve_path(gammas, o)
+        out.append((U, labels, [s["iters"] for s in stats]))
+        pr.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+
+
+def test_large_problem_needs_streamed_arrays(ccx):
+    """n = 1400 with a kNN graph: the edge arrays no longer fit beside the rows in shared memory, so
+    the streamed variant runs; parity by the fixed point's invariants (the oracle is too slow at this
+    size): with no missing data the mean of U equals the mean of X, and gamma = 0 returns X."""
+    X, _ = synth.gaussian_mixture(1400, 16, 6, seed=43)
+    pr = ccx.Problem(X, None, ccx.CCX_FP32)
+    pr.build_knn(10, phi=0.05)
+    ei, ej, w = pr.get_edges()
+    assert ei.size > 7000          # staged layout would need > 227 KB of shared memory
+    g0 = pr.fusion_scale()
+    U, labels, stats, st = pr.solve_path([0.0, 0.1 * g0, 1.0 * g0])
+    assert np.linalg.norm(U[0] - X) <= 1e-5 * np.linalg.norm(X)
+    for g in range(3):
+        assert stats[g]["converged"] in (1, 2)
+        assert np.allclose(U[g].mean(axis=0), X.mean(axis=0), atol=1e-4 * np.abs(X).max())
+
+
 def test_knn_all_pairs(ccx):
     X, _ = synth.expression_like(20, 300, 3, 40, seed=2)
     pr = ccx.Problem(X, None, ccx.CCX_FP32)
