@@ -201,6 +201,28 @@ ccx_status ccx_fusion_scale_noalloc(const ccx_problem* pr, double* gamma0);
 ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts,
                           float* U_out, int32_t* labels_out, ccx_gamma_stats* stats);
 
+/*
+ * Solve the paths of several independent problems together (each as
+ * ccx_solve_path would, from its own warm-start state; the paper treats one
+ * problem at a time, so this adds scheduling only).  Problem i runs its own
+ * iterations on its own stream with its own gammas, outputs and stats; up to
+ * max_active problems (<= 0: 32) have work queued on the GPU at once, so
+ * problems too small to fill the GPU share it.  Results are identical to
+ * solving each problem alone.
+ *   probs      : n_probs distinct handles.
+ *   gammas[i]  : host array of n_gamma[i] values for problem i.
+ *   opts       : NULL for defaults, else applied to every problem.
+ *   U_out[i], labels_out[i], stats[i] : as in ccx_solve_path for problem i
+ *               (the outer arrays themselves may be NULL: no such outputs).
+ *   status     : NULL, or n_probs entries receiving each problem's status.
+ * Returns the first hard error of any problem (its message names the problem;
+ * the other problems still run to the end), else CCX_ENOTCONV if some gamma
+ * of some problem hit max_iter, else CCX_OK.  Blocks until all are done.
+ */
+ccx_status ccx_solve_batch(ccx_problem* const* probs, int n_probs, const double* const* gammas, const int* n_gamma,
+                           const ccx_opts* opts, float* const* U_out, int32_t* const* labels_out,
+                           ccx_gamma_stats* const* stats, int max_active, ccx_status* status);
+
 /* Forget the warm-start state: the next ccx_solve_path starts from Y_0, V = 0. */
 ccx_status ccx_reset_path(ccx_problem* pr);
 

@@ -56,6 +56,7 @@ _sigs = {
     "ccx_fusion_scale": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_fusion_scale_noalloc": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
+    "ccx_solve_batch": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(Opts), _P, _P, _P, C.c_int, _P]),
     "ccx_reset_path": (C.c_int, [_P]),
     "ccx_problem_destroy": (C.c_int, [_P]),
     "ccx_time_iterations": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
@@ -196,6 +197,48 @@ def solve_path(h, gammas, n: int, p: int, opts: Opts | None = None, want_U: bool
     o = C.byref(opts) if opts is not None else None
     st = _check(_lib.ccx_solve_path(h, g.ctypes.data, G, o, up, lp, stats), allow=(0, 4))
     return U_out, labels_out, [stats[k].as_dict() for k in range(G)], st
+
+
+def solve_batch(problems, gammas_list, opts: Opts | None = None, want_U: bool = True, want_labels: bool = True,
+                device: bool = False, max_active: int = 0):
+    """Solve several problems' paths together (ccx_solve_batch).
+
+    problems: list of Problem; gammas_list: one gamma sequence per problem.  Returns
+    (U list, labels list, stats lists, per-problem status list, overall status).
+    """
+    k = len(problems)
+    gs = [np.ascontiguousarray(g, dtype=np.float64) for g in gammas_list]
+    if len(gs) != k:
+        raise ValueError("one gamma sequence per problem")
+    Us, Ls, keep = [], [], []
+    stats = [(GammaStats * max(g.size, 1))() for g in gs]
+    for pb, g in zip(problems, gs):
+        U = L = None
+        if device:
+            import torch
+            if want_U:
+                U = torch.empty((g.size, pb.n, pb.p), dtype=torch.float32, device="cuda")
+            if want_labels:
+                L = torch.empty((g.size, pb.n), dtype=torch.int32, device="cuda")
+        else:
+            if want_U:
+                U = np.empty((g.size, pb.n, pb.p), np.float32)
+            if want_labels:
+                L = np.empty((g.size, pb.n), np.int32)
+        Us.append(U)
+        Ls.append(L)
+    ptr = lambda x: 0 if x is None else (x.data_ptr() if _is_torch(x) else x.ctypes.data)
+    handles = (_P * k)(*[pb.h for pb in problems])
+    gptr = (_P * k)(*[g.ctypes.data for g in gs])
+    ng = (C.c_int * k)(*[g.size for g in gs])
+    uptr = (_P * k)(*[ptr(u) for u in Us]) if want_U else None
+    lptr = (_P * k)(*[ptr(l) for l in Ls]) if want_labels else None
+    sptr = (_P * k)(*[C.addressof(st) for st in stats])
+    status = (C.c_int * k)()
+    o = C.byref(opts) if opts is not None else None
+    st = _check(_lib.ccx_solve_batch(handles, k, gptr, ng, o, uptr, lptr, sptr, int(max_active), status),
+                allow=(0, 4))
+    return Us, Ls, [[s_[j].as_dict() for j in range(g.size)] for s_, g in zip(stats, gs)], list(status), st
 
 
 def reset_path(h) -> None:

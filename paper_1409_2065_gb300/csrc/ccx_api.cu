@@ -13,6 +13,7 @@
 #include <functional>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ccx_internal.h"
@@ -78,6 +79,7 @@ struct ccx_problem {
     cudaStream_t work = nullptr;
     cudaEvent_t ev_user = nullptr, ev_done = nullptr;
     cudaEvent_t ev_chunk[2] = {nullptr, nullptr};
+    cudaEvent_t ev_out = nullptr;    // end of one gamma's output copies
     int precision = CCX_FP32;
     int64_t n = 0, p = 0, ld_in = 0;
     int ld = 0, ldw = 0, nslices = 0, G = 0, num_sms = 0;
@@ -213,6 +215,7 @@ void free_all(ccx_problem* pr) {
     if (pr->ev_done) cudaEventDestroy(pr->ev_done);
     for (int k = 0; k < 2; ++k)
         if (pr->ev_chunk[k]) cudaEventDestroy(pr->ev_chunk[k]);
+    if (pr->ev_out) cudaEventDestroy(pr->ev_out);
     if (pr->work) cudaStreamDestroy(pr->work);
 }
 
@@ -582,9 +585,56 @@ ccx_status build_graph(ccx_problem* pr, int chunk) {
     return CCX_OK;
 }
 
+// One problem's warm-started path as a resumable sequence of steps, so that one
+// host thread can drive one problem (ccx_solve_path, blocking) or several on
+// their own streams (ccx_solve_batch, polling).  Per gamma: begin, chunks of
+// iterations with one chunk kept queued ahead of the host's check of the state
+// word, then the outputs (U, labels) and, once they have landed, the stats.
+struct PathRun {
+    ccx_problem* pr = nullptr;
+    const double* gammas = nullptr;
+    int n_gamma = 0;
+    ccx_opts o{};
+    float* U_out = nullptr;
+    int32_t* labels_out = nullptr;
+    ccx_gamma_stats* stats = nullptr;
+    bool u_dev = false, l_dev = false;
+    enum Phase { kIterate, kOutputs, kDone } phase = kDone;
+    int g = 0, launched = 0, checked = 0;
+    double rho = 0.0, eps = 0.0;
+    PdState final{};
+    std::chrono::steady_clock::time_point t0;
+    bool all_conv = true;
+};
+
 template <typename R>
-ccx_status run_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts& o, float* U_out,
-                    int32_t* labels_out, ccx_gamma_stats* stats) {
+ccx_status path_begin_gamma(PathRun& r) {
+    ccx_problem* pr = r.pr;
+    const double gamma = r.gammas[r.g];
+    r.rho = r.o.rho_scale * (pr->nyc + gamma * pr->nw);
+    if (!(r.rho > 0.0)) r.rho = r.o.rho_scale;
+    r.eps = (r.o.eps_rel * pr->nyc) * (r.o.eps_rel * pr->nyc);
+    if (!(r.eps > 0.0)) r.eps = r.o.eps_rel * r.o.eps_rel;
+    const double unit = std::is_same<R, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+    const double scale_floor = 64.0 * unit * pr->ny0;
+    r.t0 = std::chrono::steady_clock::now();
+    CUDA_TRY(launch_pd_begin_gamma<R>(make_params<R>(pr), gamma, r.rho, r.eps, r.o.tol, r.o.max_iter,
+                                      r.o.accelerate, scale_floor, pr->work));
+    r.launched = r.checked = 0;
+    r.phase = PathRun::kIterate;
+    return CCX_OK;
+}
+
+// Set-up before the first gamma (stream ordering, buffers, first iterate, graph).
+template <typename R>
+ccx_status path_open(PathRun& r) {
+    ccx_problem* pr = r.pr;
+    ccx_status s = check_limits(pr);
+    if (s != CCX_OK) return s;
+    s = enter(pr);
+    if (s != CCX_OK) return s;
+    s = ensure_path(pr);
+    if (s != CCX_OK) return s;
     IterParams<R> P = make_params<R>(pr);
     if (!pr->path_started) {
         const R* Y0 = std::is_same<R, double>::value ? reinterpret_cast<const R*>(pr->Y0d)
@@ -595,48 +645,55 @@ ccx_status run_path(ccx_problem* pr, const double* gammas, int n_gamma, const cc
     // The first launch of each kernel variant raises its shared-memory limit,
     // which must not happen under capture: launch once on a finished state
     // (done = 1, so every kernel returns at once) before capturing.
-    if (!pr->graph) CUDA_TRY(launch_pd_iteration<R>(P, pr->work));
-    {
-        ccx_status s = build_graph(pr, o.chunk);
-        if (s != CCX_OK) return s;
-    }
-    const bool u_dev = is_device_ptr(U_out);
-    const bool l_dev = is_device_ptr(labels_out);
-    bool all_conv = true;
-    for (int g = 0; g < n_gamma; ++g) {
-        const auto t0 = std::chrono::steady_clock::now();
-        const double gamma = gammas[g];
-        double rho = o.rho_scale * (pr->nyc + gamma * pr->nw);
-        if (!(rho > 0.0)) rho = o.rho_scale;
-        double eps = (o.eps_rel * pr->nyc) * (o.eps_rel * pr->nyc);
-        if (!(eps > 0.0)) eps = o.eps_rel * o.eps_rel;
-        const double unit = std::is_same<R, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
-        const double scale_floor = 64.0 * unit * pr->ny0;
-        CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, o.tol, o.max_iter, o.accelerate, scale_floor,
-                                          pr->work));
-        // chunks of iterations; one chunk stays queued ahead of the host check
-        int launched = 0, checked = 0;
-        PdState final{};
-        for (;;) {
+    if (!pr->graph || pr->graph_stream != pr->stream_edges) CUDA_TRY(launch_pd_iteration<R>(P, pr->work));
+    s = build_graph(pr, r.o.chunk);
+    if (s != CCX_OK) return s;
+    r.u_dev = is_device_ptr(r.U_out);
+    r.l_dev = is_device_ptr(r.labels_out);
+    r.g = 0;
+    r.all_conv = true;
+    r.phase = PathRun::kDone;
+    if (r.n_gamma > 0) return path_begin_gamma<R>(r);
+    return CCX_OK;
+}
+
+// Advance the run as far as the GPU allows.  With block = false nothing waits:
+// *progressed says whether anything happened.  Returns an error status, or OK
+// (the run is finished when r.phase == kDone).
+template <typename R>
+ccx_status path_step(PathRun& r, bool block, bool* progressed) {
+    ccx_problem* pr = r.pr;
+    *progressed = false;
+    if (r.phase == PathRun::kIterate) {
+        while (r.launched - r.checked < 2) {
             CUDA_TRY(cudaGraphLaunch(pr->graph, pr->work));
             count_launches(2ULL * (unsigned long long)pr->graph_chunk);
-            CUDA_TRY(cudaMemcpyAsync(&pr->st_host[launched & 1], pr->st, sizeof(PdState), cudaMemcpyDeviceToHost,
+            CUDA_TRY(cudaMemcpyAsync(&pr->st_host[r.launched & 1], pr->st, sizeof(PdState), cudaMemcpyDeviceToHost,
                                      pr->work));
-            CUDA_TRY(cudaEventRecord(pr->ev_chunk[launched & 1], pr->work));
-            ++launched;
-            if (launched - checked < 2) continue;
-            CUDA_TRY(cudaEventSynchronize(pr->ev_chunk[checked & 1]));
-            final = pr->st_host[checked & 1];
-            ++checked;
-            if (final.done) break;
+            CUDA_TRY(cudaEventRecord(pr->ev_chunk[r.launched & 1], pr->work));
+            ++r.launched;
+            *progressed = true;
         }
-        // the chunk queued behind the finished one returns at once; wait for it
-        CUDA_TRY(cudaEventSynchronize(pr->ev_chunk[checked & 1]));
-        if (final.converged == 0) all_conv = false;
-        // outputs of this gamma
-        if (U_out) {
-            float* dst = U_out + (size_t)g * pr->n * pr->ld_in;
-            if (u_dev) {
+        cudaEvent_t ev = pr->ev_chunk[r.checked & 1];
+        if (block) {
+            CUDA_TRY(cudaEventSynchronize(ev));
+        } else {
+            const cudaError_t q = cudaEventQuery(ev);
+            if (q == cudaErrorNotReady) return CCX_OK;
+            CUDA_TRY(q);
+        }
+        r.final = pr->st_host[r.checked & 1];
+        ++r.checked;
+        *progressed = true;
+        if (!r.final.done) return CCX_OK;
+        // The chunk queued behind the finished one returns at once; everything
+        // below is ordered after it on the work stream.
+        if (r.final.converged == 0) r.all_conv = false;
+        IterParams<R> P = make_params<R>(pr);
+        const int g = r.g;
+        if (r.U_out) {
+            float* dst = r.U_out + (size_t)g * pr->n * pr->ld_in;
+            if (r.u_dev) {
                 CUDA_TRY(launch_pd_finalize<R>(P, dst, pr->ld_in, (int)pr->p, pr->work));
             } else {
                 CUDA_TRY(launch_pd_finalize<R>(P, pr->Ustage, pr->p, (int)pr->p, pr->work));
@@ -644,29 +701,87 @@ ccx_status run_path(ccx_problem* pr, const double* gammas, int n_gamma, const cc
                                            sizeof(float) * pr->p, pr->n, cudaMemcpyDeviceToHost, pr->work));
             }
         }
-        int* ldst = (labels_out && l_dev) ? labels_out + (size_t)g * pr->n : pr->Lstage;
+        int* ldst = (r.labels_out && r.l_dev) ? r.labels_out + (size_t)g * pr->n : pr->Lstage;
         CUDA_TRY(launch_fused_labels((int)pr->n, P.m, pr->d_ei, pr->d_ej, pr->fused, ldst, pr->d_ncl,
                                      pr->cc_scratch, pr->work));
-        if (labels_out && !l_dev)
-            CUDA_TRY(cudaMemcpyAsync(labels_out + (size_t)g * pr->n, pr->Lstage, sizeof(int) * pr->n,
+        if (r.labels_out && !r.l_dev)
+            CUDA_TRY(cudaMemcpyAsync(r.labels_out + (size_t)g * pr->n, pr->Lstage, sizeof(int) * pr->n,
                                      cudaMemcpyDeviceToHost, pr->work));
         CUDA_TRY(cudaMemcpyAsync(pr->h_ncl, pr->d_ncl, sizeof(int), cudaMemcpyDeviceToHost, pr->work));
-        CUDA_TRY(cudaStreamSynchronize(pr->work));
-        if (stats) {
-            ccx_gamma_stats& S = stats[g];
-            S.iters = final.iter;
-            S.converged = final.converged;
-            S.n_fused = std::max(final.n_fused, 0);
-            S.n_clusters = *pr->h_ncl;
-            S.gamma = gamma;
-            S.rho = rho;
-            S.eps = eps;
-            S.d_final = final.d_last;
-            S.err_est = final.err_est;
-            S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        }
+        CUDA_TRY(cudaEventRecord(pr->ev_out, pr->work));
+        r.phase = PathRun::kOutputs;
     }
-    return all_conv ? CCX_OK : fail(CCX_ENOTCONV, "max_iter reached before convergence for some gamma");
+    if (r.phase == PathRun::kOutputs) {
+        if (block) {
+            CUDA_TRY(cudaEventSynchronize(pr->ev_out));
+        } else {
+            const cudaError_t q = cudaEventQuery(pr->ev_out);
+            if (q == cudaErrorNotReady) return CCX_OK;
+            CUDA_TRY(q);
+        }
+        *progressed = true;
+        if (r.stats) {
+            ccx_gamma_stats& S = r.stats[r.g];
+            S.iters = r.final.iter;
+            S.converged = r.final.converged;
+            S.n_fused = std::max(r.final.n_fused, 0);
+            S.n_clusters = *pr->h_ncl;
+            S.gamma = r.gammas[r.g];
+            S.rho = r.rho;
+            S.eps = r.eps;
+            S.d_final = r.final.d_last;
+            S.err_est = r.final.err_est;
+            S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t0).count();
+        }
+        ++r.g;
+        if (r.g < r.n_gamma) return path_begin_gamma<R>(r);
+        r.phase = PathRun::kDone;
+    }
+    return CCX_OK;
+}
+
+ccx_status path_open_any(PathRun& r) {
+    return r.pr->precision == CCX_FP64 ? path_open<double>(r) : path_open<float>(r);
+}
+
+ccx_status path_step_any(PathRun& r, bool block, bool* progressed) {
+    return r.pr->precision == CCX_FP64 ? path_step<double>(r, block, progressed)
+                                       : path_step<float>(r, block, progressed);
+}
+
+// Final status of a run that reached kDone, after its stream ordering is closed.
+ccx_status path_close(PathRun& r, ccx_status run_status) {
+    std::string keep = g_err;
+    const ccx_status l = leave(r.pr);
+    if (run_status != CCX_OK) {
+        g_err = keep;
+        return run_status;
+    }
+    if (l != CCX_OK) return l;
+    if (!r.all_conv) return fail(CCX_ENOTCONV, "max_iter reached before convergence for some gamma");
+    return CCX_OK;
+}
+
+// Options of one solve, validated; the FP64 default tolerance is tighter.
+ccx_status resolve_opts(const ccx_problem* pr, const ccx_opts* opts, ccx_opts* o) {
+    ccx_opts_default(o);
+    if (pr->precision == CCX_FP64) o->tol = 1e-10;
+    if (opts) *o = *opts;
+    if (!(o->rho_scale > 0.0) || !std::isfinite(o->rho_scale)) return fail(CCX_EINVAL, "rho_scale must be > 0");
+    if (!(o->eps_rel > 0.0) || !std::isfinite(o->eps_rel)) return fail(CCX_EINVAL, "eps_rel must be > 0");
+    if (!(o->tol > 0.0)) return fail(CCX_EINVAL, "tol must be > 0");
+    if (o->max_iter < 1) return fail(CCX_EINVAL, "max_iter must be >= 1");
+    if (o->chunk < 1 || o->chunk > 4096) return fail(CCX_EINVAL, "chunk must be in [1, 4096]");
+    return CCX_OK;
+}
+
+ccx_status check_gammas(const double* gammas, int n_gamma) {
+    if (n_gamma < 0) return fail(CCX_EINVAL, "n_gamma < 0");
+    if (n_gamma > 0 && !gammas) return fail(CCX_EINVAL, "gammas is NULL");
+    for (int g = 0; g < n_gamma; ++g)
+        if (!std::isfinite(gammas[g]) || gammas[g] < 0.0)
+            return fail(CCX_EINVAL, "gammas[%d] must be finite and >= 0", g);
+    return CCX_OK;
 }
 
 }  // namespace
@@ -726,6 +841,7 @@ ccx_status ccx_problem_create(const float* X, const uint8_t* mask, int64_t n, in
     TRY(cudaEventCreateWithFlags(&pr->ev_done, cudaEventDisableTiming));
     TRY(cudaEventCreateWithFlags(&pr->ev_chunk[0], cudaEventDisableTiming));
     TRY(cudaEventCreateWithFlags(&pr->ev_chunk[1], cudaEventDisableTiming));
+    TRY(cudaEventCreateWithFlags(&pr->ev_out, cudaEventDisableTiming));
     TRY(cudaEventRecord(pr->ev_user, pr->user));
     TRY(cudaStreamWaitEvent(pr->work, pr->ev_user, 0));
     const size_t nl = (size_t)n * pr->ld;
@@ -893,36 +1009,107 @@ ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, co
                           int32_t* labels_out, ccx_gamma_stats* stats) {
     g_err.clear();
     if (!pr) return fail(CCX_EINVAL, "problem is NULL");
-    if (n_gamma < 0) return fail(CCX_EINVAL, "n_gamma < 0");
-    if (n_gamma > 0 && !gammas) return fail(CCX_EINVAL, "gammas is NULL");
-    for (int g = 0; g < n_gamma; ++g)
-        if (!std::isfinite(gammas[g]) || gammas[g] < 0.0)
-            return fail(CCX_EINVAL, "gammas[%d] must be finite and >= 0", g);
-    ccx_opts o;
-    ccx_opts_default(&o);
-    if (pr->precision == CCX_FP64) o.tol = 1e-10;
-    if (opts) o = *opts;
-    pr->stream_edges = o.stream_edges ? 1 : 0;
-    if (!(o.rho_scale > 0.0) || !std::isfinite(o.rho_scale)) return fail(CCX_EINVAL, "rho_scale must be > 0");
-    if (!(o.eps_rel > 0.0) || !std::isfinite(o.eps_rel)) return fail(CCX_EINVAL, "eps_rel must be > 0");
-    if (!(o.tol > 0.0)) return fail(CCX_EINVAL, "tol must be > 0");
-    if (o.max_iter < 1) return fail(CCX_EINVAL, "max_iter must be >= 1");
-    if (o.chunk < 1 || o.chunk > 4096) return fail(CCX_EINVAL, "chunk must be in [1, 4096]");
-    ccx_status s = check_limits(pr);
+    ccx_status s = check_gammas(gammas, n_gamma);
     if (s != CCX_OK) return s;
-    s = enter(pr);
+    PathRun r;
+    s = resolve_opts(pr, opts, &r.o);
     if (s != CCX_OK) return s;
-    s = ensure_path(pr);
+    pr->stream_edges = r.o.stream_edges ? 1 : 0;
+    r.pr = pr;
+    r.gammas = gammas;
+    r.n_gamma = n_gamma;
+    r.U_out = U_out;
+    r.labels_out = labels_out;
+    r.stats = stats;
+    s = path_open_any(r);
     if (s != CCX_OK) return s;
-    ccx_status r = pr->precision == CCX_FP64 ? run_path<double>(pr, gammas, n_gamma, o, U_out, labels_out, stats)
-                                             : run_path<float>(pr, gammas, n_gamma, o, U_out, labels_out, stats);
-    std::string keep = g_err;
-    ccx_status l = leave(pr);
-    if (r != CCX_OK) {
-        g_err = keep;
-        return r;
+    while (s == CCX_OK && r.phase != PathRun::kDone) {
+        bool progressed = false;
+        s = path_step_any(r, true, &progressed);
     }
-    return l;
+    return path_close(r, s);
+}
+
+ccx_status ccx_solve_batch(ccx_problem* const* probs, int n_probs, const double* const* gammas, const int* n_gamma,
+                           const ccx_opts* opts, float* const* U_out, int32_t* const* labels_out,
+                           ccx_gamma_stats* const* stats, int max_active, ccx_status* status) {
+    g_err.clear();
+    if (n_probs < 0) return fail(CCX_EINVAL, "n_probs < 0");
+    if (n_probs == 0) return CCX_OK;
+    if (!probs || !gammas || !n_gamma) return fail(CCX_EINVAL, "probs, gammas and n_gamma must not be NULL");
+    for (int i = 0; i < n_probs; ++i) {
+        if (!probs[i]) return fail(CCX_EINVAL, "probs[%d] is NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (probs[j] == probs[i]) return fail(CCX_EINVAL, "probs[%d] and probs[%d] are the same problem", j, i);
+        ccx_status s = check_gammas(gammas[i], n_gamma[i]);
+        if (s != CCX_OK) return fail(s, "problem %d: %s", i, g_err.c_str());
+    }
+    if (max_active <= 0) max_active = 32;
+    std::vector<PathRun> runs(n_probs);
+    std::vector<ccx_status> st(n_probs, CCX_OK);
+    std::vector<std::string> msg(n_probs);
+    for (int i = 0; i < n_probs; ++i) {
+        PathRun& r = runs[i];
+        ccx_status s = resolve_opts(probs[i], opts, &r.o);
+        if (s != CCX_OK) return fail(s, "problem %d: %s", i, g_err.c_str());
+        r.pr = probs[i];
+        r.gammas = gammas[i];
+        r.n_gamma = n_gamma[i];
+        r.U_out = U_out ? U_out[i] : nullptr;
+        r.labels_out = labels_out ? labels_out[i] : nullptr;
+        r.stats = stats ? stats[i] : nullptr;
+    }
+    // Problems run on their own work streams; up to max_active of them have
+    // chunks queued at once, so small problems share the GPU.  The host polls
+    // without blocking and sleeps briefly when no run moved.
+    std::vector<int> active;
+    int next = 0, finished = 0;
+    auto retire = [&](int i, ccx_status s) {
+        st[i] = path_close(runs[i], s);
+        if (st[i] != CCX_OK) msg[i] = g_err;
+        ++finished;
+    };
+    while (finished < n_probs) {
+        while ((int)active.size() < max_active && next < n_probs) {
+            const int i = next++;
+            g_err.clear();
+            runs[i].pr->stream_edges = runs[i].o.stream_edges ? 1 : 0;
+            const ccx_status s = path_open_any(runs[i]);
+            if (s != CCX_OK) {
+                st[i] = s;
+                msg[i] = g_err;
+                ++finished;
+                continue;
+            }
+            if (runs[i].phase == PathRun::kDone) retire(i, CCX_OK);
+            else active.push_back(i);
+        }
+        bool any = false;
+        for (size_t a = 0; a < active.size();) {
+            const int i = active[a];
+            bool progressed = false;
+            g_err.clear();
+            const ccx_status s = path_step_any(runs[i], false, &progressed);
+            any = any || progressed;
+            if (s != CCX_OK || runs[i].phase == PathRun::kDone) {
+                retire(i, s);
+                active.erase(active.begin() + (long)a);
+            } else {
+                ++a;
+            }
+        }
+        if (!any && !active.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    ccx_status worst = CCX_OK;
+    int first = -1;
+    for (int i = 0; i < n_probs; ++i) {
+        if (status) status[i] = st[i];
+        if (st[i] != CCX_OK && st[i] != CCX_ENOTCONV && first < 0) first = i;
+        if (st[i] == CCX_ENOTCONV && worst == CCX_OK) worst = CCX_ENOTCONV;
+    }
+    if (first >= 0) return fail(st[first], "problem %d: %s", first, msg[first].c_str());
+    if (worst == CCX_ENOTCONV) return fail(CCX_ENOTCONV, "max_iter reached before convergence for some gamma");
+    return CCX_OK;
 }
 
 ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts, double* slice_ms,
