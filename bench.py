@@ -202,6 +202,60 @@ def run_reference(args, rank, ws, dist):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- batched problems
+def batch_specs(count, nmax, pmax, seed=3):
+    """Sizes of the batched workload: n ~ U[50, nmax], p ~ U[10, pmax], 2-8 Gaussian clusters
+    (means ~ N(0, 9 I), noise N(0, I)), problem i drawn with seed 1000 * seed + i."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(1000 * seed + i)
+        n = int(rng.integers(50, nmax + 1))
+        p = int(rng.integers(10, pmax + 1))
+        k = int(rng.integers(2, 9))
+        X, _ = synth.gaussian_mixture(n, p, k, seed=1000 * seed + i)
+        out.append(X)
+    return out
+
+
+def run_batch(args, ccx, torch, rank):
+    Xs = batch_specs(args.batch, args.batch_nmax, args.batch_pmax)
+
+    def make():
+        probs = []
+        for X in Xs:
+            pr = ccx.Problem(torch.from_numpy(X).cuda())
+            pr.build_knn(10, phi_auto=True, normalize=True)
+            probs.append(pr)
+        return probs
+
+    probs = make()
+    grids = [synth.log_grid(0.03 * pr.fusion_scale(), 3.0 * pr.fusion_scale(), args.batch_gammas) for pr in probs]
+    # one call per problem, one after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [pr.solve_path(g, device=True) for pr, g in zip(probs, grids)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    iters = sum(s["iters"] for r in seq for s in r[2])
+    for pr in probs:
+        pr.reset_path()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Us, Ls, stats, status, _ = ccx.solve_batch(probs, grids, device=True, max_active=args.batch)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    same = all(torch.equal(Us[i], seq[i][0]) and torch.equal(Ls[i], seq[i][1]) for i in range(len(probs)))
+    sz = [X.shape for X in Xs]
+    line = {"metric": "gamma-path solves/s", "workload": f"{args.batch} problems, n~U[50,{args.batch_nmax}], "
+            f"p~U[10,{args.batch_pmax}], 2-8 clusters, kNN k=10, {args.batch_gammas} gammas in [0.03,3]*gamma0",
+            "sequential": len(probs) / t_seq, "batched": len(probs) / t_bat, "speedup": t_seq / t_bat,
+            "seconds_sequential": t_seq, "seconds_batched": t_bat, "mm_iterations": int(iters),
+            "sum_np": int(sum(n * p for n, p in sz)), "identical_results": bool(same), "dtype": "f32",
+            "data": "synthetic"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -213,6 +267,13 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, metavar="P",
+                    help="instead of the default step: P independent problems from the batched-workload size "
+                         "distribution (scaled by --batch-nmax/--batch-pmax), solved one call after another and "
+                         "then together with ccx_solve_batch; prints the two solve rates")
+    ap.add_argument("--batch-nmax", type=int, default=2000)
+    ap.add_argument("--batch-pmax", type=int, default=5000)
+    ap.add_argument("--batch-gammas", type=int, default=30)
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -227,6 +288,9 @@ def main():
     import paper_1409_2065_gb300 as ccx
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.batch:
+        run_batch(args, ccx, torch, rank)
+        return
     W = workload(args.workload)
     n, p = W["X"].shape
     Xd = torch.from_numpy(W["X"]).cuda()
