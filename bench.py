@@ -256,6 +256,61 @@ def run_batch(args, ccx, torch, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, ccx, torch, rank):
+    Xs = batch_specs(args.serve_jobs, args.batch_nmax, args.batch_pmax, seed=4)
+    rng = np.random.default_rng(4)
+    gaps = rng.exponential(1.0 / args.serve, size=len(Xs))
+
+    def arm(max_active):
+        probs = []
+        for X in Xs:
+            pr = ccx.Problem(torch.from_numpy(X).cuda())
+            pr.build_knn(10, phi_auto=True, normalize=True)
+            probs.append(pr)
+        grids = [synth.log_grid(0.03 * pr.fusion_scale(), 3.0 * pr.fusion_scale(), args.batch_gammas)
+                 for pr in probs]
+        torch.cuda.synchronize()
+        srv = ccx.Server(max_active=max_active)
+        arrive, done, results = [0.0] * len(Xs), [0.0] * len(Xs), [None] * len(Xs)
+
+        def waiter(i, t):
+            st, U, L, stats = srv.wait(t, -1)
+            done[i] = time.perf_counter()
+            results[i] = (U, L)
+
+        threads = []
+        t0 = time.perf_counter()
+        due = t0
+        for i, pr in enumerate(probs):
+            due += gaps[i]
+            time.sleep(max(0.0, due - time.perf_counter()))
+            arrive[i] = time.perf_counter()
+            th = threading.Thread(target=waiter, args=(i, srv.submit(pr, grids[i], device=True)))
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        wall = max(done) - t0
+        srv.close()
+        lat = sorted(d - a for d, a in zip(done, arrive))
+        q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+        for pr in probs:
+            pr.close()
+        return {"p50_s": q(0.5), "p99_s": q(0.99), "solves_per_s": len(Xs) / wall, "wall_s": wall}, results
+
+    served, r1 = arm(32)
+    plain, r2 = arm(1)
+    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(r1, r2))
+    line = {"metric": "served gamma-path solves/s and latency", "rate_jobs_per_s": args.serve,
+            "workload": f"{len(Xs)} jobs, Poisson arrivals, n~U[50,{args.batch_nmax}], p~U[10,{args.batch_pmax}], "
+                        f"2-8 clusters, kNN k=10, {args.batch_gammas} gammas in [0.03,3]*gamma0",
+            "continuous_batching": served, "one_at_a_time": plain,
+            "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"],
+            "identical_results": bool(same), "dtype": "f32", "data": "synthetic"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -271,6 +326,11 @@ def main():
                     help="instead of the default step: P independent problems from the batched-workload size "
                          "distribution (scaled by --batch-nmax/--batch-pmax), solved one call after another and "
                          "then together with ccx_solve_batch; prints the two solve rates")
+    ap.add_argument("--serve", type=float, default=0.0, metavar="RATE",
+                    help="instead of the default step: Poisson arrivals of --serve-jobs jobs at RATE jobs/s "
+                         "(sizes as --batch), served by ccx_server with continuous batching and, for comparison, "
+                         "one job at a time; prints p50/p99 latency and solve rates")
+    ap.add_argument("--serve-jobs", type=int, default=64)
     ap.add_argument("--batch-nmax", type=int, default=2000)
     ap.add_argument("--batch-pmax", type=int, default=5000)
     ap.add_argument("--batch-gammas", type=int, default=30)
@@ -290,6 +350,9 @@ def main():
     torch.cuda.set_device(local)
     if args.batch:
         run_batch(args, ccx, torch, rank)
+        return
+    if args.serve > 0:
+        run_serve(args, ccx, torch, rank)
         return
     W = workload(args.workload)
     n, p = W["X"].shape

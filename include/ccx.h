@@ -41,6 +41,7 @@ extern "C" {
 #endif
 
 typedef struct ccx_problem ccx_problem;
+typedef struct ccx_server ccx_server;
 
 typedef enum {
     CCX_OK = 0,
@@ -200,6 +201,38 @@ ccx_status ccx_fusion_scale_noalloc(const ccx_problem* pr, double* gamma0);
  */
 ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts,
                           float* U_out, int32_t* labels_out, ccx_gamma_stats* stats);
+
+/*
+ * Serving: a background scheduler that runs submitted path solves while the
+ * caller keeps submitting (the paper has no serving layer; each job is one
+ * ccx_solve_path).  Jobs that arrive while others are on the GPU are admitted
+ * as running jobs finish and device memory frees up: a job starts when fewer
+ * than max_active jobs run and the estimated iteration buffers of the running
+ * jobs plus its own fit in hbm_budget bytes (0: 80 % of the device memory free
+ * at creation); the first job always starts.  Running jobs share the GPU as in
+ * ccx_solve_batch, and each job's result equals solving it alone.
+ *   ccx_server_create : opts as in ccx_solve_path (NULL: defaults), applied to
+ *                       every job; max_active <= 0 means 32.  Starts one host
+ *                       thread, which makes all CUDA calls for the jobs.
+ *   ccx_submit        : queues the path of problem pr over gammas (copied);
+ *                       outputs as in ccx_solve_path.  The caller must not use
+ *                       pr or the output buffers until ccx_wait has returned
+ *                       for the ticket.  One job per problem at a time
+ *                       (CCX_EINVAL otherwise).  When the job ends, the
+ *                       problem's iteration buffers are released, so its next
+ *                       solve starts from U_0 = Y_0.
+ *   ccx_wait          : waits up to timeout_ms (< 0: no limit) and returns the
+ *                       job's status, or CCX_ETIMEOUT while it still runs (wait
+ *                       again later).  Never blocks beyond the limit.  A ticket
+ *                       is released by the call that returns its status.
+ *   ccx_server_destroy: jobs not yet started end with CCX_ECANCELLED; running
+ *                       jobs finish first.  Wait for every ticket before.
+ */
+ccx_status ccx_server_create(const ccx_opts* opts, size_t hbm_budget, int max_active, ccx_server** out);
+ccx_status ccx_submit(ccx_server* srv, ccx_problem* pr, const double* gammas, int n_gamma, float* U_out,
+                      int32_t* labels_out, ccx_gamma_stats* stats, uint64_t* ticket);
+ccx_status ccx_wait(ccx_server* srv, uint64_t ticket, int64_t timeout_ms);
+ccx_status ccx_server_destroy(ccx_server* srv);
 
 /*
  * Solve the paths of several independent problems together (each as

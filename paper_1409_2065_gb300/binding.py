@@ -57,6 +57,10 @@ _sigs = {
     "ccx_fusion_scale_noalloc": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
     "ccx_solve_batch": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(Opts), _P, _P, _P, C.c_int, _P]),
+    "ccx_server_create": (C.c_int, [C.POINTER(Opts), C.c_size_t, C.c_int, C.POINTER(_P)]),
+    "ccx_submit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, C.POINTER(C.c_uint64)]),
+    "ccx_wait": (C.c_int, [_P, C.c_uint64, C.c_int64]),
+    "ccx_server_destroy": (C.c_int, [_P]),
     "ccx_reset_path": (C.c_int, [_P]),
     "ccx_problem_destroy": (C.c_int, [_P]),
     "ccx_time_iterations": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
@@ -239,6 +243,57 @@ def solve_batch(problems, gammas_list, opts: Opts | None = None, want_U: bool = 
     st = _check(_lib.ccx_solve_batch(handles, k, gptr, ng, o, uptr, lptr, sptr, int(max_active), status),
                 allow=(0, 4))
     return Us, Ls, [[s_[j].as_dict() for j in range(g.size)] for s_, g in zip(stats, gs)], list(status), st
+
+
+class Server:
+    """Background scheduler of path solves (ccx_server_*).  submit() returns a ticket;
+    wait(ticket) returns (status, U, labels, stats) once the job is done."""
+
+    def __init__(self, opts: Opts | None = None, hbm_budget: int = 0, max_active: int = 0):
+        h = _P()
+        o = C.byref(opts) if opts is not None else None
+        _check(_lib.ccx_server_create(o, int(hbm_budget), int(max_active), C.byref(h)))
+        self.h = h.value
+        self._jobs = {}
+
+    def submit(self, problem, gammas, device: bool = False):
+        g = np.ascontiguousarray(gammas, dtype=np.float64)
+        G = g.size
+        if device:
+            import torch
+            U = torch.empty((G, problem.n, problem.p), dtype=torch.float32, device="cuda")
+            L = torch.empty((G, problem.n), dtype=torch.int32, device="cuda")
+            up, lp = U.data_ptr(), L.data_ptr()
+        else:
+            U = np.empty((G, problem.n, problem.p), np.float32)
+            L = np.empty((G, problem.n), np.int32)
+            up, lp = U.ctypes.data, L.ctypes.data
+        stats = (GammaStats * max(G, 1))()
+        t = C.c_uint64(0)
+        _check(_lib.ccx_submit(self.h, problem.h, g.ctypes.data, G, up, lp, stats, C.byref(t)))
+        self._jobs[t.value] = (g, U, L, stats, problem)
+        return t.value
+
+    def wait(self, ticket, timeout_ms: int = -1):
+        st = _lib.ccx_wait(self.h, int(ticket), int(timeout_ms))
+        if st == 5:
+            return st, None, None, None
+        if st not in (0, 4):
+            self._jobs.pop(ticket, None)
+            raise CcxError(st, last_error())
+        g, U, L, stats, _ = self._jobs.pop(ticket)
+        return st, U, L, [stats[k].as_dict() for k in range(g.size)]
+
+    def close(self):
+        if self.h:
+            _check(_lib.ccx_server_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def reset_path(h) -> None:

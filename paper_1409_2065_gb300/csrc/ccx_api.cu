@@ -14,6 +14,10 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
 #include <vector>
 
 #include "ccx_internal.h"
@@ -1109,6 +1113,224 @@ ccx_status ccx_solve_batch(ccx_problem* const* probs, int n_probs, const double*
     }
     if (first >= 0) return fail(st[first], "problem %d: %s", first, msg[first].c_str());
     if (worst == CCX_ENOTCONV) return fail(CCX_ENOTCONV, "max_iter reached before convergence for some gamma");
+    return CCX_OK;
+}
+
+// ------------------------------------------------------------------ serving
+namespace {
+
+// Device bytes ensure_path allocates for a problem's iteration (admission estimate).
+size_t path_bytes(const ccx_problem* pr) {
+    const bool fp64 = pr->precision == CCX_FP64;
+    const size_t es = fp64 ? 8 : 4;
+    const size_t nl = (size_t)pr->n * pr->ld;
+    const size_t m = pr->ei.size();
+    const size_t nsl = (size_t)((pr->p + kSliceCols - 1) / kSliceCols);
+    const size_t G = std::min<size_t>(nsl, (size_t)std::max(pr->num_sms, 1));
+    const size_t T = kSliceThreads;
+    size_t b = 4 * es * nl + (fp64 ? 0 : 2 * 4 * nl) + (pr->has_mask ? 2 * es * nl : 0);
+    b += 2 * es * 2 * ((size_t)pr->la + pr->le) * T;
+    b += G * (size_t)pr->le * T * 4 + G * 64 + m * 9 + 16 * (size_t)pd_reduce_blocks(pr->le);
+    b += (size_t)pr->n * pr->p * 4 + (size_t)pr->n * 8 + 4096;
+    return b + b / 16 + (1u << 20);   // allocation rounding
+}
+
+}  // namespace
+
+struct ccx_server {
+    struct Job {
+        uint64_t ticket = 0;
+        ccx_problem* pr = nullptr;
+        std::vector<double> gammas;
+        float* U_out = nullptr;
+        int32_t* labels_out = nullptr;
+        ccx_gamma_stats* stats = nullptr;
+        size_t bytes = 0;
+        PathRun run;
+        bool done = false;
+        ccx_status status = CCX_OK;
+        std::string msg;
+    };
+    ccx_opts opts{};
+    size_t budget = 0;
+    int max_active = 32;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Job>> pending;
+    std::map<uint64_t, std::shared_ptr<Job>> jobs;   // submitted and not yet waited for
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+
+    void finish(const std::shared_ptr<Job>& j, ccx_status st, const std::string& m) {
+        std::lock_guard<std::mutex> lk(mu);
+        j->status = st;
+        j->msg = m;
+        j->done = true;
+        cv_done.notify_all();
+    }
+
+    // The scheduler: admits queued jobs while the estimated device memory of
+    // the running ones stays within the budget (one job always runs), steps
+    // every running job without blocking, and releases a job's iteration
+    // buffers when it finishes.
+    void loop() {
+        cudaSetDevice(device);
+        std::vector<std::shared_ptr<Job>> active;
+        size_t used = 0;
+        for (;;) {
+            std::vector<std::shared_ptr<Job>> admitted;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (active.empty() && pending.empty()) {
+                    if (stop) break;
+                    cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+                    continue;
+                }
+                while (!pending.empty() && (int)active.size() < max_active) {
+                    auto& j = pending.front();
+                    if (!active.empty() && used + j->bytes > budget) break;
+                    used += j->bytes;
+                    active.push_back(j);
+                    admitted.push_back(j);
+                    pending.pop_front();
+                }
+            }
+            for (auto& j : admitted) {
+                g_err.clear();
+                j->pr->stream_edges = j->run.o.stream_edges ? 1 : 0;
+                const ccx_status st = path_open_any(j->run);
+                if (st != CCX_OK || j->run.phase == PathRun::kDone) {
+                    const ccx_status fin = st != CCX_OK ? st : path_close(j->run, CCX_OK);
+                    const std::string m = g_err;
+                    free_path(j->pr);
+                    used -= j->bytes;
+                    active.erase(std::find(active.begin(), active.end(), j));
+                    finish(j, fin, m);
+                }
+            }
+            bool any = false;
+            for (size_t a = 0; a < active.size();) {
+                auto j = active[a];
+                bool progressed = false;
+                g_err.clear();
+                ccx_status st = path_step_any(j->run, false, &progressed);
+                any = any || progressed;
+                if (st != CCX_OK || j->run.phase == PathRun::kDone) {
+                    st = path_close(j->run, st);
+                    const std::string m = g_err;
+                    free_path(j->pr);
+                    used -= j->bytes;
+                    active.erase(active.begin() + (long)a);
+                    finish(j, st, m);
+                } else {
+                    ++a;
+                }
+            }
+            if (!any) {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait_for(lk, std::chrono::microseconds(20));
+            }
+        }
+    }
+};
+
+ccx_status ccx_server_create(const ccx_opts* opts, size_t hbm_budget, int max_active, ccx_server** out) {
+    g_err.clear();
+    if (!out) return fail(CCX_EINVAL, "out is NULL");
+    *out = nullptr;
+    auto srv = std::make_unique<ccx_server>();
+    ccx_opts_default(&srv->opts);
+    if (opts) srv->opts = *opts;
+    CUDA_TRY(cudaGetDevice(&srv->device));
+    if (hbm_budget == 0) {
+        size_t fr = 0, tot = 0;
+        CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        hbm_budget = fr / 5 * 4;
+    }
+    srv->budget = hbm_budget;
+    srv->max_active = max_active > 0 ? max_active : 32;
+    ccx_server* raw = srv.get();
+    try {
+        srv->worker = std::thread([raw] { raw->loop(); });
+    } catch (...) {
+        return fail(CCX_ENOMEM, "could not start the server thread");
+    }
+    *out = srv.release();
+    return CCX_OK;
+}
+
+ccx_status ccx_submit(ccx_server* srv, ccx_problem* pr, const double* gammas, int n_gamma, float* U_out,
+                      int32_t* labels_out, ccx_gamma_stats* stats, uint64_t* ticket) {
+    g_err.clear();
+    if (!srv || !pr || !ticket) return fail(CCX_EINVAL, "NULL argument");
+    ccx_status s = check_gammas(gammas, n_gamma);
+    if (s != CCX_OK) return s;
+    auto j = std::make_shared<ccx_server::Job>();
+    s = resolve_opts(pr, &srv->opts, &j->run.o);
+    if (s != CCX_OK) return s;
+    j->pr = pr;
+    j->gammas.assign(gammas, gammas + n_gamma);
+    j->U_out = U_out;
+    j->labels_out = labels_out;
+    j->stats = stats;
+    j->bytes = path_bytes(pr);
+    j->run.pr = pr;
+    j->run.n_gamma = n_gamma;
+    j->run.U_out = U_out;
+    j->run.labels_out = labels_out;
+    j->run.stats = stats;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stop) return fail(CCX_ECANCELLED, "server is shutting down");
+        for (auto& kv : srv->jobs)
+            if (kv.second->pr == pr && !kv.second->done)
+                return fail(CCX_EINVAL, "problem already has a job in flight (ticket %llu)",
+                            (unsigned long long)kv.first);
+        j->ticket = srv->next_ticket++;
+        j->run.gammas = j->gammas.data();
+        srv->jobs[j->ticket] = j;
+        srv->pending.push_back(j);
+        *ticket = j->ticket;
+    }
+    srv->cv_work.notify_one();
+    return CCX_OK;
+}
+
+ccx_status ccx_wait(ccx_server* srv, uint64_t ticket, int64_t timeout_ms) {
+    g_err.clear();
+    if (!srv) return fail(CCX_EINVAL, "server is NULL");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return fail(CCX_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    std::shared_ptr<ccx_server::Job> j = it->second;
+    auto ready = [&] { return j->done; };
+    if (timeout_ms < 0) srv->cv_done.wait(lk, ready);
+    else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return fail(CCX_ETIMEOUT, "job %llu still running", (unsigned long long)ticket);
+    srv->jobs.erase(ticket);
+    if (j->status != CCX_OK) g_err = j->msg;
+    return j->status;
+}
+
+ccx_status ccx_server_destroy(ccx_server* srv) {
+    g_err.clear();
+    if (!srv) return CCX_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        for (auto& j : srv->pending) {
+            j->status = CCX_ECANCELLED;
+            j->msg = "server destroyed before the job started";
+            j->done = true;
+        }
+        srv->pending.clear();
+    }
+    srv->cv_work.notify_all();
+    srv->cv_done.notify_all();
+    if (srv->worker.joinable()) srv->worker.join();
+    delete srv;
     return CCX_OK;
 }
 
