@@ -50,6 +50,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 __all__ = [
+    "min_connected_k",
     "EdgeGraph",
     "fill_missing",
     "pd_constants",
@@ -361,3 +362,31 @@ def fusion_scale(X, mask, ei, ej, w) -> float:
     Y = fill_missing(X, mask)
     dist = np.sqrt(np.sum((Y[np.asarray(ei)] - Y[np.asarray(ej)]) ** 2, axis=1))
     return float(np.median(dist / (2.0 * np.asarray(w, dtype=np.float64))))
+
+
+def min_connected_k(X, mask, k_max: int) -> int:
+    """Smallest k in [1, k_max] whose k-nearest-neighbour union graph is connected
+    (Calibration of Weights: i ~_k j when either is among the other's k nearest,
+    distances on the rows with missing entries at observed column means, ties
+    to the smaller index; complete coalescence needs a connected graph, and the
+    paper proposes searching k for connectivity).  0 when no k <= k_max works.
+
+    A plain scan over k = 1, 2, ... with union-find components; the neighbour
+    order of every row is computed once in FP64.
+    """
+    Y = fill_missing(X, mask)
+    n = Y.shape[0]
+    if n < 2:
+        raise ValueError("need at least two cases")
+    kmax = min(int(k_max), n - 1)
+    order = []
+    for i in range(n):
+        diff = Y - Y[i]
+        d2 = np.einsum("jk,jk->j", diff, diff)
+        order.append([j for _, j in sorted((d2[j], j) for j in range(n) if j != i)])
+    for k in range(1, kmax + 1):
+        ei = [i for i in range(n) for j in order[i][:k]]
+        ej = [j for i in range(n) for j in order[i][:k]]
+        if int(fused_labels(n, ei, ej, np.ones(len(ei), bool)).max()) == 0:
+            return k
+    return 0

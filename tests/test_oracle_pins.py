@@ -315,3 +315,39 @@ def test_fused_labels_canonical():
     lab = O.fused_labels(6, [0, 1, 2, 3], [1, 2, 4, 5], [False, True, False, True])
     # components: {0}, {1,2}, {3,5}, {4}
     assert lab.tolist() == [0, 1, 1, 2, 3, 2]
+
+
+def test_min_connected_k_two_clusters_closed_form():
+    """Two tight clusters far apart: a case of the smaller cluster (size a) reaches the other
+    cluster only among its a nearest, so the union graph connects exactly at k = min(a, b)."""
+    rng = np.random.default_rng(4)
+    for a, b in [(4, 7), (6, 6), (9, 3)]:
+        X = np.vstack([rng.normal(0.0, 0.1, (a, 3)), rng.normal(50.0, 0.1, (b, 3))])
+        assert O.min_connected_k(X, None, 20) == min(a, b)
+        assert O.min_connected_k(X, None, min(a, b) - 1) == 0
+
+
+def test_min_connected_k_chain_and_brute_force():
+    # equally spaced points: each case's nearest neighbour (ties to the smaller index) links a chain
+    X = np.arange(10, dtype=np.float64)[:, None]
+    assert O.min_connected_k(X, None, 5) == 1
+    # random data: the first connected k from an independent construction (scipy distances,
+    # stable argsort, scipy connected components)
+    sp = pytest.importorskip("scipy.sparse.csgraph")
+    from scipy.spatial.distance import cdist
+    from scipy.sparse import coo_matrix
+    for seed in range(3):
+        X, _ = synth.gaussian_mixture(45, 4, 4, seed=seed)
+        D = cdist(X.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+        np.fill_diagonal(D, np.inf)
+        order = np.argsort(D, axis=1, kind="stable")
+        want = 0
+        for k in range(1, 44):
+            rows = np.repeat(np.arange(45), k)
+            cols = order[:, :k].ravel()
+            ncomp = sp.connected_components(coo_matrix((np.ones(rows.size), (rows, cols)), shape=(45, 45)),
+                                            directed=False)[0]
+            if ncomp == 1:
+                want = k
+                break
+        assert O.min_connected_k(X, None, 44) == want
