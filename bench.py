@@ -334,6 +334,9 @@ def main():
     ap.add_argument("--batch-nmax", type=int, default=2000)
     ap.add_argument("--batch-pmax", type=int, default=5000)
     ap.add_argument("--batch-gammas", type=int, default=30)
+    ap.add_argument("--min-k", type=int, default=0, metavar="KMAX",
+                    help="instead of the default step: time the search for the smallest k <= KMAX whose kNN "
+                         "graph of the workload is connected, on the GPU and with the oracle")
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -364,6 +367,21 @@ def main():
     m = int(ei.size)
     gammas = gamma_grid(W, pr.fusion_scale())
     G = len(gammas)
+    if args.min_k:
+        pr.min_connected_k(args.min_k)                      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k_gpu = pr.min_connected_k(args.min_k)
+        torch.cuda.synchronize()
+        t_gpu = time.perf_counter() - t0
+        import oracle as O
+        t0 = time.perf_counter()
+        k_ref = O.min_connected_k(W["X"].astype(np.float64), W["mask"], args.min_k)
+        t_ref = time.perf_counter() - t0
+        print(json.dumps({"metric": "seconds to the smallest connected k", "workload": W["desc"], "k_max": args.min_k,
+                          "k": k_gpu, "oracle_k": k_ref, "gpu_seconds": t_gpu, "oracle_seconds": t_ref,
+                          "oracle_cores": os.cpu_count()}), flush=True)
+        return
     if args.iterations_only:
         slice_ms, reduce_ms = pr.time_iterations(float(gammas[len(gammas) // 2]), args.iterations_only)
         print(json.dumps({"workload": W["desc"], "iterations": args.iterations_only, "slice_ms": slice_ms,

@@ -144,6 +144,19 @@ ccx_status ccx_set_edges(ccx_problem* pr, int64_t n_edges, const int32_t* ei, co
 ccx_status ccx_build_knn(ccx_problem* pr, const ccx_knn_rule* rule);
 
 /*
+ * Smallest k in [1, k_max] for which the kNN union graph of the rule above
+ * (i ~_k j; distances on the rows with missing entries at observed column
+ * means, ties to the smaller index) is connected, i.e. for which the path can
+ * end in complete coalescence (Calibration of Weights: the paper proposes
+ * finding this k by bisection with a graph search).  *k_out = 0 when even
+ * k_max (capped at n - 1) leaves the graph disconnected.  The neighbour lists
+ * for k_max are built once on the GPU; each bisection probe runs the GPU
+ * connected-components pass on their k-prefix.  The problem's edge set is not
+ * changed.  CCX_EINVAL for k_max < 1 or n < 2.
+ */
+ccx_status ccx_min_connected_k(ccx_problem* pr, int k_max, int* k_out);
+
+/*
  * Copy the current edge set out (host arrays, sorted by (ei, ej)).  With
  * ei == NULL only *n_edges is written (size query).  Otherwise *n_edges must
  * hold the capacity on entry and receives the count.

@@ -53,6 +53,7 @@ _sigs = {
     "ccx_set_edges": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "ccx_build_knn": (C.c_int, [_P, C.POINTER(KnnRule)]),
     "ccx_get_edges": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P]),
+    "ccx_min_connected_k": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "ccx_fusion_scale": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_fusion_scale_noalloc": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
@@ -150,6 +151,13 @@ def set_edges(h, ei, ej, w) -> None:
 def build_knn(h, k: int, phi: float = 0.0, phi_auto: bool = False, normalize: bool = False) -> None:
     r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)))
     _check(_lib.ccx_build_knn(h, C.byref(r)))
+
+
+def min_connected_k(h, k_max: int) -> int:
+    """Smallest k <= k_max whose kNN union graph is connected (0 if none)."""
+    k = C.c_int(0)
+    _check(_lib.ccx_min_connected_k(h, int(k_max), C.byref(k)))
+    return k.value
 
 
 def get_edges(h):
@@ -327,6 +335,9 @@ class Problem:
 
     def get_edges(self):
         return get_edges(self.h)
+
+    def min_connected_k(self, k_max):
+        return min_connected_k(self.h, k_max)
 
     def fusion_scale(self):
         return fusion_scale(self.h)

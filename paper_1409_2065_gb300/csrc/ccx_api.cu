@@ -938,6 +938,23 @@ ccx_status ccx_build_knn(ccx_problem* pr, const ccx_knn_rule* rule) {
     return leave(pr);
 }
 
+ccx_status ccx_min_connected_k(ccx_problem* pr, int k_max, int* k_out) {
+    g_err.clear();
+    if (!pr || !k_out) return fail(CCX_EINVAL, "NULL argument");
+    if (k_max < 1) return fail(CCX_EINVAL, "k_max must be >= 1");
+    if (pr->n < 2) return fail(CCX_EINVAL, "need at least two cases");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    knn_set_exact_rows(pr->Xf, pr->has_mask ? pr->maskbits : nullptr, pr->colmean, pr->ldw);
+    std::string err;
+    int probes = 0;
+    const cudaError_t e =
+        knn_min_connected_k(pr->Y0f, (int)pr->n, (int)pr->p, pr->ld, k_max, pr->work, k_out, &probes, &err);
+    if (e == cudaErrorNotSupported) return fail(CCX_EUNSUPPORTED, "%s", err.c_str());
+    if (e != cudaSuccess) return fail(CCX_ECUDA, "connectivity search failed: %s", cudaGetErrorString(e));
+    return leave(pr);
+}
+
 ccx_status ccx_get_edges(const ccx_problem* pr, int64_t* n_edges, int32_t* ei, int32_t* ej, double* w) {
     g_err.clear();
     if (!pr || !n_edges) return fail(CCX_EINVAL, "NULL argument");

@@ -166,6 +166,10 @@ struct KnnResult {
 };
 cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
                       cudaStream_t s, KnnResult* out, std::string* err);
+// smallest k in [1, k_max] whose kNN union graph is connected (0: none), by
+// bisection over GPU connected components of the k-prefix of the neighbour lists
+cudaError_t knn_min_connected_k(const float* Y0f, int n, int p, int ld, int k_max, cudaStream_t s, int* k_out,
+                                int* probes, std::string* err);
 cudaError_t edge_distances(const float* Y0f, int n, int p, int ld, const int* ei_d, const int* ej_d, int m,
                            double* d2_d, cudaStream_t s);
 

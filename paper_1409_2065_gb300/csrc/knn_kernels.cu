@@ -247,19 +247,12 @@ void knn_set_exact_rows(const float* Xf, const uint32_t* bits, const double* col
     g_knn_args = {Xf, bits, colmean, ldw};
 }
 
-cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
-                      cudaStream_t s, KnnResult* out, std::string* err) {
+// The k nearest neighbours of every row on the device: nbr (n x kk) and their
+// exact squared distances nd2, each row ascending by (d2, j).  The caller frees
+// *nbr and *nd2.
+static cudaError_t knn_lists(const float* Y0f, int n, int p, int ld, int kk, cudaStream_t s, int** nbr_out,
+                             double** nd2_out) {
     const KnnDeviceArgs ka = g_knn_args;
-    if (n > 4096) {
-        *err = "kNN build supports n <= 4096 in this build";
-        return cudaErrorNotSupported;
-    }
-    const int kk = std::min(k, n - 1);
-    out->ei.clear();
-    out->ej.clear();
-    out->w.clear();
-    out->d2.clear();
-    if (kk <= 0) return cudaSuccess;
     const int use_all = (kk >= n - 1) ? 1 : 0;
     cudaError_t e;
     double* sq = nullptr;
@@ -305,6 +298,113 @@ cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi,
     knn_row_kernel<<<n, kRowThreads, smem, s>>>(ka.Xf, ka.bits, ka.colmean, sq, G, gunit, use_all, n, p, ld, ka.ldw,
                                                 kk, npow2, nbr, nd2);
     if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(), e;
+    cudaFree(sq);
+    cudaFree(G);
+    *nbr_out = nbr;
+    *nd2_out = nd2;
+    return cudaSuccess;
+}
+
+// edges (i, nbr[i][r]) for r < k of the neighbour lists (kk per row)
+__global__ void probe_edges_kernel(const int* __restrict__ nbr, int n, int kk, int k, int* __restrict__ ei,
+                                   int* __restrict__ ej) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n * k) return;
+    const int i = q / k, r = q - i * k;
+    ei[q] = i;
+    ej[q] = nbr[(size_t)i * kk + r];
+}
+
+__global__ void fill_ones_kernel(uint8_t* f, int m) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < m) f[q] = 1;
+}
+
+cudaError_t knn_min_connected_k(const float* Y0f, int n, int p, int ld, int k_max, cudaStream_t s, int* k_out,
+                                int* probes, std::string* err) {
+    *k_out = 0;
+    *probes = 0;
+    if (n > 4096) {
+        *err = "kNN build supports n <= 4096 in this build";
+        return cudaErrorNotSupported;
+    }
+    const int kk = std::min(k_max, n - 1);
+    if (kk <= 0) return cudaSuccess;
+    int* nbr = nullptr;
+    double* nd2 = nullptr;
+    cudaError_t e = knn_lists(Y0f, n, p, ld, kk, s, &nbr, &nd2);
+    if (e != cudaSuccess) return e;
+    const size_t mmax = (size_t)n * kk;
+    int *ei = nullptr, *ej = nullptr, *lab = nullptr, *scratch = nullptr, *ncl = nullptr;
+    uint8_t* ones = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(nbr);
+        cudaFree(nd2);
+        cudaFree(ei);
+        cudaFree(ej);
+        cudaFree(lab);
+        cudaFree(scratch);
+        cudaFree(ncl);
+        cudaFree(ones);
+    };
+    if ((e = cudaMalloc(&ei, sizeof(int) * mmax)) != cudaSuccess) return cleanup(), e;
+    if ((e = cudaMalloc(&ej, sizeof(int) * mmax)) != cudaSuccess) return cleanup(), e;
+    if ((e = cudaMalloc(&ones, mmax)) != cudaSuccess) return cleanup(), e;
+    if ((e = cudaMalloc(&lab, sizeof(int) * n)) != cudaSuccess) return cleanup(), e;
+    if ((e = cudaMalloc(&scratch, sizeof(int) * n)) != cudaSuccess) return cleanup(), e;
+    if ((e = cudaMalloc(&ncl, sizeof(int))) != cudaSuccess) return cleanup(), e;
+    count_launches(1);
+    fill_ones_kernel<<<(int)((mmax + 255) / 256), 256, 0, s>>>(ones, (int)mmax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(), e;
+    // the union graph only grows with k, so its connectivity is monotone in k: bisection
+    auto connected = [&](int k, bool* yes) -> cudaError_t {
+        const int m = n * k;
+        count_launches(1);
+        probe_edges_kernel<<<(m + 255) / 256, 256, 0, s>>>(nbr, n, kk, k, ei, ej);
+        cudaError_t r = cudaGetLastError();
+        if (r == cudaSuccess) r = launch_fused_labels(n, m, ei, ej, ones, lab, ncl, scratch, s);
+        int h = 0;
+        if (r == cudaSuccess) r = cudaMemcpyAsync(&h, ncl, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+        *yes = (h == 1);
+        ++*probes;
+        return r;
+    };
+    bool yes = false;
+    if ((e = connected(kk, &yes)) != cudaSuccess) return cleanup(), e;
+    if (!yes) return cleanup(), cudaSuccess;
+    int lo = 1, hi = kk;   // connected at hi
+    while (lo < hi) {
+        const int mid = lo + (hi - lo) / 2;
+        if ((e = connected(mid, &yes)) != cudaSuccess) return cleanup(), e;
+        if (yes) hi = mid;
+        else lo = mid + 1;
+    }
+    *k_out = hi;
+    cleanup();
+    return cudaSuccess;
+}
+
+cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
+                      cudaStream_t s, KnnResult* out, std::string* err) {
+    if (n > 4096) {
+        *err = "kNN build supports n <= 4096 in this build";
+        return cudaErrorNotSupported;
+    }
+    const int kk = std::min(k, n - 1);
+    out->ei.clear();
+    out->ej.clear();
+    out->w.clear();
+    out->d2.clear();
+    if (kk <= 0) return cudaSuccess;
+    int* nbr = nullptr;
+    double* nd2 = nullptr;
+    cudaError_t e = knn_lists(Y0f, n, p, ld, kk, s, &nbr, &nd2);
+    if (e != cudaSuccess) return e;
+    auto cleanup = [&]() {
+        cudaFree(nbr);
+        cudaFree(nd2);
+    };
     std::vector<int> hn((size_t)n * kk);
     std::vector<double> hd((size_t)n * kk);
     if ((e = cudaMemcpyAsync(hn.data(), nbr, sizeof(int) * hn.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

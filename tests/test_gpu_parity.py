@@ -171,6 +171,20 @@ def test_large_problem_needs_streamed_arrays(ccx):
         assert np.allclose(U[g].mean(axis=0), X.mean(axis=0), atol=1e-4 * np.abs(X).max())
 
 
+@pytest.mark.parametrize("n,p,frac", [(60, 5, 0.0), (300, 40, 0.05), (700, 300, 0.0)])
+def test_min_connected_k_matches_oracle(ccx, n, p, frac):
+    """Bisection over GPU connected components gives the oracle's linear-scan answer exactly."""
+    X, _ = synth.gaussian_mixture(n, p, 5, seed=n + p)
+    mask = synth.random_mask(np.random.default_rng(n), n, p, frac) if frac > 0 else None
+    pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+    for k_max in (3, 40):
+        assert pr.min_connected_k(k_max) == O.min_connected_k(X.astype(np.float64), mask, k_max)
+    # two far clusters: connects exactly at the smaller cluster's size
+    rng = np.random.default_rng(1)
+    Xc = np.vstack([rng.normal(0, 0.1, (13, 4)), rng.normal(40, 0.1, (30, 4))]).astype(np.float32)
+    assert ccx.Problem(Xc).min_connected_k(50) == 13
+
+
 def test_knn_all_pairs(ccx):
     X, _ = synth.expression_like(20, 300, 3, 40, seed=2)
     pr = ccx.Problem(X, None, ccx.CCX_FP32)
