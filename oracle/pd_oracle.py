@@ -45,11 +45,15 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import math
+
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
 __all__ = [
+    "geo_distance",
+    "knn_composite_weights",
     "min_connected_k",
     "EdgeGraph",
     "fill_missing",
@@ -390,3 +394,70 @@ def min_connected_k(X, mask, k_max: int) -> int:
         if int(fused_labels(n, ei, ej, np.ones(len(ei), bool)).max()) == 0:
             return k
     return 0
+
+
+def geo_distance(c1, c2, geodesic: bool) -> float:
+    """Geographic distance in degrees between (latitude, longitude) pairs given in degrees.
+
+    geodesic=False: Euclidean norm of the coordinate difference with the
+    longitude difference taken modulo 360 (Calibration of Weights: the
+    components of y_i - y_j are computed in modulo arithmetic);
+    geodesic=True: great-circle central angle (the alternative the paper
+    suggests), from the spherical case of Vincenty's formula (an atan2 of the
+    cross and dot products of the two unit vectors, accurate from coincident
+    points to antipodes), in degrees of arc.
+    """
+    lat1, lon1 = float(c1[0]), float(c1[1])
+    lat2, lon2 = float(c2[0]), float(c2[1])
+    if not geodesic:
+        dl = math.fmod(abs(lon1 - lon2), 360.0)
+        if dl > 180.0:
+            dl = 360.0 - dl
+        dp = lat1 - lat2
+        return math.sqrt(dp * dp + dl * dl)
+    r = math.pi / 180.0
+    p1, p2, dl = lat1 * r, lat2 * r, (lon2 - lon1) * r
+    y = math.hypot(math.cos(p2) * math.sin(dl), math.cos(p1) * math.sin(p2) - math.sin(p1) * math.cos(p2) * math.cos(dl))
+    x = math.sin(p1) * math.sin(p2) + math.cos(p1) * math.cos(p2) * math.cos(dl)
+    return math.atan2(y, x) / r
+
+
+def knn_composite_weights(X, mask, coords, alpha: float, k: int, phi, normalize: bool, geodesic: bool = False):
+    """kNN union graph and Gaussian-kernel weights on the composite distance
+    d_ij = alpha ||x_i - x_j|| + (1 - alpha) g_ij (Calibration of Weights, the
+    composite genetic + geographic distance), g from geo_distance; otherwise
+    the rule of knn_gaussian_weights: k nearest by d (ties to the smaller
+    index), union, w = exp(-phi d^2), phi "auto" = 1 / median d^2 over the
+    union edges, optional normalisation over i < j, zero weights dropped.
+    Returns (ei, ej, w, d2) with d2 = d^2, i < j sorted by (i, j).
+    """
+    Y = fill_missing(X, mask)
+    C = np.asarray(coords, dtype=np.float64)
+    n = Y.shape[0]
+    D = np.empty((n, n))
+    for i in range(n):
+        diff = Y - Y[i]
+        dg = np.sqrt(np.einsum("jk,jk->j", diff, diff))
+        for j in range(n):
+            D[i, j] = alpha * dg[j] + (1.0 - alpha) * geo_distance(C[i], C[j], geodesic)
+    kk = min(k, n - 1)
+    pairs = set()
+    for i in range(n):
+        order = sorted((D[i, j], j) for j in range(n) if j != i)
+        for _, j in order[:kk]:
+            pairs.add((min(i, j), max(i, j)))
+    pairs = sorted(pairs)
+    ei = np.array([a for a, _ in pairs], dtype=np.int64)
+    ej = np.array([b for _, b in pairs], dtype=np.int64)
+    d = D[ei, ej] if ei.size else np.zeros(0)
+    d2 = d * d
+    if isinstance(phi, str):
+        med = float(np.median(d2)) if d2.size else 0.0
+        phi = 1.0 / med if med > 0 else 0.0
+    if normalize and d2.size:
+        w = np.exp(-phi * (d2 - d2.min()))
+        w = w / w.sum()
+    else:
+        w = np.exp(-phi * d2)
+    keep = w > 0.0
+    return ei[keep], ej[keep], w[keep], d2[keep], phi

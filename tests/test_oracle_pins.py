@@ -351,3 +351,45 @@ def test_min_connected_k_chain_and_brute_force():
                 want = k
                 break
         assert O.min_connected_k(X, None, 44) == want
+
+
+def test_geo_distance_geometry():
+    """Geographic distances pinned by geometry, not by the formulas."""
+    g = O.geo_distance
+    # modulo arithmetic: longitudes 179 and -179 are 2 degrees apart; differences never exceed 180
+    assert g((0, 179), (0, -179), False) == pytest.approx(2.0, abs=1e-12)
+    assert g((3, 0), (-1, 540), False) == pytest.approx(np.hypot(4, 180), abs=1e-12)
+    assert g((10, -20), (13, -16), False) == pytest.approx(5.0, abs=1e-12)
+    # great circles: along a meridian or the equator the arc is the coordinate difference
+    assert g((10, 40), (55, 40), True) == pytest.approx(45.0, abs=1e-10)
+    assert g((0, 170), (0, -170), True) == pytest.approx(20.0, abs=1e-10)
+    # the pole is 90 degrees from every equator point; antipodes are 180 apart
+    for lon in (-120.0, 0.0, 33.0):
+        assert g((90, 0), (0, lon), True) == pytest.approx(90.0, abs=1e-10)
+    assert g((10, 20), (-10, -160), True) == pytest.approx(180.0, abs=1e-9)
+    # an octant: the three axis points are pairwise 90 degrees apart
+    pts = [(0, 0), (0, 90), (90, 0)]
+    for a in range(3):
+        for b in range(a + 1, 3):
+            assert g(pts[a], pts[b], True) == pytest.approx(90.0, abs=1e-10)
+    # short arcs at latitude 60 shrink the longitude difference by cos(60) = 1/2
+    assert g((60, 0), (60, 0.001), True) == pytest.approx(0.0005, rel=1e-6)
+
+
+def test_composite_weights_special_cases():
+    X, _ = synth.gaussian_mixture(30, 6, 3, seed=8)
+    rng = np.random.default_rng(9)
+    coords = np.c_[rng.uniform(-60, 60, 30), rng.uniform(-180, 180, 30)]
+    # alpha = 1: the Euclidean rule of Eq. 8 exactly
+    a = O.knn_composite_weights(X, None, coords, 1.0, 4, 0.2, True)
+    b = O.knn_gaussian_weights(X, None, 4, 0.2, True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.allclose(a[2], b[2], rtol=1e-12) and np.allclose(a[3], b[3], rtol=1e-12)
+    # alpha = 0 with identical genotypes: neighbours by geography alone.  Four cases on the
+    # equator at longitudes -179, 179, 10, 20: the pairs across the date line and 10-20 are nearest
+    Xs = np.zeros((4, 3))
+    cs = np.array([[0.0, -179.0], [0.0, 179.0], [0.0, 10.0], [0.0, 20.0]])
+    for geodesic in (False, True):
+        ei, ej, w, d2, _ = O.knn_composite_weights(Xs, None, cs, 0.0, 1, 0.0, False, geodesic)
+        assert list(zip(ei.tolist(), ej.tolist())) == [(0, 1), (2, 3)]
+        assert np.allclose(d2, [4.0, 100.0], rtol=1e-12)
