@@ -144,6 +144,24 @@ ccx_status ccx_set_edges(ccx_problem* pr, int64_t n_edges, const int32_t* ei, co
 ccx_status ccx_build_knn(ccx_problem* pr, const ccx_knn_rule* rule);
 
 /*
+ * The kNN Gaussian-kernel rule above on the composite genetic + geographic
+ * distance d_ij = alpha ||y_i - y_j|| + (1 - alpha) g_ij (Calibration of
+ * Weights): neighbours, phi (phi_auto: 1 / median d^2 over the union edges),
+ * weights exp(-phi d^2) and the normalisation all use d.
+ *   coords  : host array of n (latitude, longitude) pairs in degrees,
+ *             latitude in [-90, 90].
+ *   alpha   : in [0, 1]; 1 gives ccx_build_knn.
+ *   geodesic: 0: g = Euclidean norm of the coordinate difference in degrees,
+ *             longitude difference taken modulo 360; 1: g = great-circle
+ *             angle in degrees.
+ * Candidates come from the tensor-core Gram with a bound that covers its
+ * rounding; their distances, and g, are then computed exactly in double.
+ * Replaces any earlier edge set.
+ */
+ccx_status ccx_build_knn_composite(ccx_problem* pr, const ccx_knn_rule* rule, const double* coords, double alpha,
+                                   int geodesic);
+
+/*
  * Smallest k in [1, k_max] for which the kNN union graph of the rule above
  * (i ~_k j; distances on the rows with missing entries at observed column
  * means, ties to the smaller index) is connected, i.e. for which the path can

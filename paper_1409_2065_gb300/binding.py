@@ -54,6 +54,7 @@ _sigs = {
     "ccx_build_knn": (C.c_int, [_P, C.POINTER(KnnRule)]),
     "ccx_get_edges": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P]),
     "ccx_min_connected_k": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "ccx_build_knn_composite": (C.c_int, [_P, C.POINTER(KnnRule), _P, C.c_double, C.c_int]),
     "ccx_fusion_scale": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_fusion_scale_noalloc": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
@@ -151,6 +152,14 @@ def set_edges(h, ei, ej, w) -> None:
 def build_knn(h, k: int, phi: float = 0.0, phi_auto: bool = False, normalize: bool = False) -> None:
     r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)))
     _check(_lib.ccx_build_knn(h, C.byref(r)))
+
+
+def build_knn_composite(h, k: int, coords, alpha: float, phi: float = 0.0, phi_auto: bool = False,
+                        normalize: bool = False, geodesic: bool = False) -> None:
+    """kNN weights on alpha * genetic + (1 - alpha) * geographic distance; coords: n x 2 (lat, lon) degrees."""
+    r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)))
+    c = np.ascontiguousarray(coords, dtype=np.float64)
+    _check(_lib.ccx_build_knn_composite(h, C.byref(r), c.ctypes.data, float(alpha), int(bool(geodesic))))
 
 
 def min_connected_k(h, k_max: int) -> int:
@@ -338,6 +347,9 @@ class Problem:
 
     def min_connected_k(self, k_max):
         return min_connected_k(self.h, k_max)
+
+    def build_knn_composite(self, k, coords, alpha, phi=0.0, phi_auto=False, normalize=False, geodesic=False):
+        build_knn_composite(self.h, k, coords, alpha, phi, phi_auto, normalize, geodesic)
 
     def fusion_scale(self):
         return fusion_scale(self.h)

@@ -938,6 +938,38 @@ ccx_status ccx_build_knn(ccx_problem* pr, const ccx_knn_rule* rule) {
     return leave(pr);
 }
 
+ccx_status ccx_build_knn_composite(ccx_problem* pr, const ccx_knn_rule* rule, const double* coords, double alpha,
+                                   int geodesic) {
+    g_err.clear();
+    if (!pr || !rule || !coords) return fail(CCX_EINVAL, "NULL argument");
+    if (rule->k < 1) return fail(CCX_EINVAL, "k must be >= 1");
+    if (!rule->phi_auto && (!std::isfinite(rule->phi) || rule->phi < 0.0))
+        return fail(CCX_EINVAL, "phi must be finite and >= 0");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(CCX_EINVAL, "alpha must be in [0, 1]");
+    for (int64_t i = 0; i < pr->n; ++i) {
+        const double la = coords[2 * i], lo = coords[2 * i + 1];
+        if (!std::isfinite(la) || !std::isfinite(lo) || la < -90.0 || la > 90.0)
+            return fail(CCX_EINVAL, "coords[%lld]: latitude must be in [-90, 90] and both finite", (long long)i);
+    }
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    double* geo = nullptr;
+    CUDA_TRY(dalloc(&geo, 2 * (size_t)pr->n));
+    cudaError_t e = cudaMemcpyAsync(geo, coords, sizeof(double) * 2 * pr->n, cudaMemcpyHostToDevice, pr->work);
+    knn_set_exact_rows(pr->Xf, pr->has_mask ? pr->maskbits : nullptr, pr->colmean, pr->ldw);
+    KnnResult res;
+    std::string err;
+    if (e == cudaSuccess)
+        e = knn_build(pr->Y0f, (int)pr->n, (int)pr->p, pr->ld, rule->k, rule->phi, rule->phi_auto, rule->normalize,
+                      pr->work, &res, &err, geo, alpha, geodesic ? 1 : 0);
+    cudaFree(geo);
+    if (e == cudaErrorNotSupported) return fail(CCX_EUNSUPPORTED, "%s", err.c_str());
+    if (e != cudaSuccess) return fail(CCX_ECUDA, "kNN build failed: %s", cudaGetErrorString(e));
+    s = install_edges(pr, res.ei, res.ej, res.w);
+    if (s != CCX_OK) return s;
+    return leave(pr);
+}
+
 ccx_status ccx_min_connected_k(ccx_problem* pr, int k_max, int* k_out) {
     g_err.clear();
     if (!pr || !k_out) return fail(CCX_EINVAL, "NULL argument");

@@ -164,8 +164,11 @@ struct KnnResult {
     std::vector<double> w, d2;
     double phi = 0.0;
 };
+// geo: NULL (Euclidean rule), or device (latitude, longitude) pairs in degrees for the
+// composite distance alpha ||y_i - y_j|| + (1 - alpha) g_ij (geodesic: great-circle g)
 cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
-                      cudaStream_t s, KnnResult* out, std::string* err);
+                      cudaStream_t s, KnnResult* out, std::string* err, const double* geo = nullptr,
+                      double alpha = 1.0, int geodesic = 0);
 // smallest k in [1, k_max] whose kNN union graph is connected (0: none), by
 // bisection over GPU connected components of the k-prefix of the neighbour lists
 cudaError_t knn_min_connected_k(const float* Y0f, int n, int p, int ld, int k_max, cudaStream_t s, int* k_out,

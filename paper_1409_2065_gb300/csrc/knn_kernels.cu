@@ -121,14 +121,34 @@ __device__ void bitonic_sort(double* key, int* idx, int len_pow2) {
     }
 }
 
+// Geographic distance in degrees between (latitude, longitude) pairs in
+// degrees: the coordinate difference with longitude modulo 360 (Calibration of
+// Weights), or the great-circle angle from the spherical case of Vincenty's
+// formula (atan2 of the cross and dot products; accurate up to antipodes).
+__device__ double geo_deg(const double* __restrict__ geo, int i, int j, int geodesic) {
+    const double lat1 = geo[2 * i], lon1 = geo[2 * i + 1], lat2 = geo[2 * j], lon2 = geo[2 * j + 1];
+    if (!geodesic) {
+        double dl = fmod(fabs(lon1 - lon2), 360.0);
+        if (dl > 180.0) dl = 360.0 - dl;
+        const double dp = lat1 - lat2;
+        return sqrt(dp * dp + dl * dl);
+    }
+    const double r = 3.14159265358979323846 / 180.0;
+    const double p1 = lat1 * r, p2 = lat2 * r, dl = (lon2 - lon1) * r;
+    const double y = hypot(cos(p2) * sin(dl), cos(p1) * sin(p2) - sin(p1) * cos(p2) * cos(dl));
+    const double x = sin(p1) * sin(p2) + cos(p1) * cos(p2) * cos(dl);
+    return atan2(y, x) / r;
+}
+
 __global__ void __launch_bounds__(kRowThreads) knn_row_kernel(
     const float* __restrict__ Xf, const uint32_t* __restrict__ bits, const double* __restrict__ colmean,
     const double* __restrict__ sq, const float* __restrict__ G, double gunit, int use_all, int n, int p, int ld,
-    int ldw, int k, int npow2, int* __restrict__ nbr, double* __restrict__ nd2) {
+    int ldw, int k, int npow2, int* __restrict__ nbr, double* __restrict__ nd2, const double* __restrict__ geo,
+    double alpha, int geodesic) {
     extern __shared__ __align__(16) unsigned char sm[];
     double* key = reinterpret_cast<double*>(sm);          // npow2
-    double* av = key + npow2;                             // n: approx a_ij
-    double* bv = av + n;                                  // n: bound b_ij
+    double* av = key + npow2;                             // n: lower bound of the distance key
+    double* bv = av + n;                                  // n: upper bound of the distance key
     int* idx = reinterpret_cast<int*>(bv + n);            // npow2
     int* cand = idx + npow2;                              // n
     __shared__ int ncand;
@@ -143,8 +163,15 @@ __global__ void __launch_bounds__(kRowThreads) knn_row_kernel(
             const double a = sqi + sq[j] - 2.0 * (double)G[(size_t)i * n + j];
             // |G_ij - <y_i, y_j>| <= gunit * ||y_i|| ||y_j||; d2 = sq_i + sq_j - 2 <y_i, y_j>
             const double b = 2.0 * gunit * nri * sqrt(sq[j]) * (1.0 + 1e-9) + 1e-300;
-            av[j] = a;
-            bv[j] = b;
+            if (geo) {
+                // composite key alpha ||y_i - y_j|| + (1 - alpha) g_ij, g exact in double
+                const double g = (1.0 - alpha) * geo_deg(geo, i, j, geodesic);
+                av[j] = (alpha * sqrt(fmax(a - b, 0.0)) + g) * (1.0 - 1e-12);
+                bv[j] = (alpha * sqrt(fmax(a + b, 0.0)) + g) * (1.0 + 1e-12) + 1e-300;
+            } else {
+                av[j] = a - b;      // squared-distance key
+                bv[j] = a + b;
+            }
         }
     }
     __syncthreads();
@@ -152,7 +179,7 @@ __global__ void __launch_bounds__(kRowThreads) knn_row_kernel(
         if (threadIdx.x == 0) Tsh = INFINITY;
     } else {
         for (int t = threadIdx.x; t < npow2; t += blockDim.x) {
-            key[t] = (t < n && t != i) ? av[t] + bv[t] : INFINITY;
+            key[t] = (t < n && t != i) ? bv[t] : INFINITY;
             idx[t] = t;
         }
         __syncthreads();
@@ -162,9 +189,9 @@ __global__ void __launch_bounds__(kRowThreads) knn_row_kernel(
     if (threadIdx.x == 0) ncand = 0;
     __syncthreads();
     const double T = Tsh;
-    // candidates: a - b <= T (order fixed later by the sort)
+    // candidates: lower bound <= T (order fixed later by the sort)
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        if (j != i && (use_all || av[j] - bv[j] <= T)) {
+        if (j != i && (use_all || av[j] <= T)) {
             const int slot = atomicAdd(&ncand, 1);
             cand[slot] = j;
         }
@@ -185,7 +212,8 @@ __global__ void __launch_bounds__(kRowThreads) knn_row_kernel(
             s += dd * dd;
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) av[j] = s;   // av now holds exact d2 for candidates
+        // av now holds the exact key of each candidate: d2, or the composite distance
+        if (lane == 0) av[j] = geo ? alpha * sqrt(s) + (1.0 - alpha) * geo_deg(geo, i, j, geodesic) : s;
     }
     __syncthreads();
     int cp2 = 1;
@@ -203,7 +231,7 @@ __global__ void __launch_bounds__(kRowThreads) knn_row_kernel(
     bitonic_sort(key, idx, cp2);
     for (int r = threadIdx.x; r < k; r += blockDim.x) {
         nbr[(size_t)i * k + r] = idx[r];
-        nd2[(size_t)i * k + r] = key[r];
+        nd2[(size_t)i * k + r] = geo ? key[r] * key[r] : key[r];   // squared distance for the weights
     }
 }
 
@@ -251,7 +279,7 @@ void knn_set_exact_rows(const float* Xf, const uint32_t* bits, const double* col
 // exact squared distances nd2, each row ascending by (d2, j).  The caller frees
 // *nbr and *nd2.
 static cudaError_t knn_lists(const float* Y0f, int n, int p, int ld, int kk, cudaStream_t s, int** nbr_out,
-                             double** nd2_out) {
+                             double** nd2_out, const double* geo = nullptr, double alpha = 1.0, int geodesic = 0) {
     const KnnDeviceArgs ka = g_knn_args;
     const int use_all = (kk >= n - 1) ? 1 : 0;
     cudaError_t e;
@@ -296,7 +324,7 @@ static cudaError_t knn_lists(const float* Y0f, int n, int p, int ld, int kk, cud
         return cleanup(), e;
     count_launches(1);
     knn_row_kernel<<<n, kRowThreads, smem, s>>>(ka.Xf, ka.bits, ka.colmean, sq, G, gunit, use_all, n, p, ld, ka.ldw,
-                                                kk, npow2, nbr, nd2);
+                                                kk, npow2, nbr, nd2, geo, alpha, geodesic);
     if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(), e;
     cudaFree(sq);
     cudaFree(G);
@@ -386,7 +414,8 @@ cudaError_t knn_min_connected_k(const float* Y0f, int n, int p, int ld, int k_ma
 }
 
 cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
-                      cudaStream_t s, KnnResult* out, std::string* err) {
+                      cudaStream_t s, KnnResult* out, std::string* err, const double* geo, double alpha,
+                      int geodesic) {
     if (n > 4096) {
         *err = "kNN build supports n <= 4096 in this build";
         return cudaErrorNotSupported;
@@ -399,7 +428,7 @@ cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi,
     if (kk <= 0) return cudaSuccess;
     int* nbr = nullptr;
     double* nd2 = nullptr;
-    cudaError_t e = knn_lists(Y0f, n, p, ld, kk, s, &nbr, &nd2);
+    cudaError_t e = knn_lists(Y0f, n, p, ld, kk, s, &nbr, &nd2, geo, alpha, geodesic);
     if (e != cudaSuccess) return e;
     auto cleanup = [&]() {
         cudaFree(nbr);

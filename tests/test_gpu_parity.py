@@ -185,6 +185,24 @@ def test_min_connected_k_matches_oracle(ccx, n, p, frac):
     assert ccx.Problem(Xc).min_connected_k(50) == 13
 
 
+@pytest.mark.parametrize("alpha,geodesic,frac", [(0.7, False, 0.0), (0.3, True, 0.05), (0.05, True, 0.0)])
+def test_knn_composite_matches_oracle(ccx, alpha, geodesic, frac):
+    """Composite genetic + geographic kNN weights: exact edge set and weights against brute force."""
+    n, p = 150, 40
+    X, mask, _ = synth.genotype_like(n, p, 4, seed=51, fst=0.05, frac_missing=frac)
+    if frac == 0.0:
+        mask = None
+    rng = np.random.default_rng(52)
+    coords = np.c_[rng.uniform(-70, 70, n), rng.uniform(-180, 180, n)]
+    pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+    pr.build_knn_composite(6, coords, alpha, phi_auto=True, normalize=True, geodesic=geodesic)
+    ei, ej, w = pr.get_edges()
+    oei, oej, ow, _, _ = O.knn_composite_weights(X.astype(np.float64), mask, coords, alpha, 6, "auto", True,
+                                                 geodesic)
+    assert np.array_equal(ei, oei) and np.array_equal(ej, oej)
+    assert np.allclose(w, ow, rtol=1e-10, atol=0)
+
+
 def test_knn_all_pairs(ccx):
     X, _ = synth.expression_like(20, 300, 3, 40, seed=2)
     pr = ccx.Problem(X, None, ccx.CCX_FP32)
