@@ -337,6 +337,10 @@ def main():
     ap.add_argument("--min-k", type=int, default=0, metavar="KMAX",
                     help="instead of the default step: time the search for the smallest k <= KMAX whose kNN "
                          "graph of the workload is connected, on the GPU and with the oracle")
+    ap.add_argument("--composite", type=float, default=-1.0, metavar="ALPHA",
+                    help="instead of the default step: time the kNN weights on the composite distance "
+                         "ALPHA * genetic + (1 - ALPHA) * great-circle distance (sampling sites synthetic: one "
+                         "site per population plus 2-degree jitter), on the GPU and with the oracle")
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -367,6 +371,32 @@ def main():
     m = int(ei.size)
     gammas = gamma_grid(W, pr.fusion_scale())
     G = len(gammas)
+    if args.composite >= 0.0:
+        rng = np.random.default_rng(5)
+        pops = 5
+        sites = np.c_[rng.uniform(-50, 60, pops), rng.uniform(-180, 180, pops)]
+        who = np.arange(n) * pops // n                      # cases are stored population by population
+        coords = sites[who] + rng.normal(0.0, 2.0, (n, 2))
+        coords[:, 0] = np.clip(coords[:, 0], -90.0, 90.0)
+        kw = dict(phi_auto=True, normalize=True, geodesic=True)
+        pr.build_knn_composite(W["k"], coords, args.composite, **kw)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr.build_knn_composite(W["k"], coords, args.composite, **kw)
+        torch.cuda.synchronize()
+        t_gpu = time.perf_counter() - t0
+        ei, ej, w = pr.get_edges()
+        import oracle as O
+        t0 = time.perf_counter()
+        oei, oej, ow, _, _ = O.knn_composite_weights(W["X"].astype(np.float64), W["mask"], coords, args.composite,
+                                                     W["k"], "auto", True, True)
+        t_ref = time.perf_counter() - t0
+        same = bool(np.array_equal(ei, oei) and np.array_equal(ej, oej) and np.allclose(w, ow, rtol=1e-10))
+        print(json.dumps({"metric": "seconds per composite-distance kNN weight build", "workload": W["desc"],
+                          "alpha": args.composite, "edges": int(ei.size), "gpu_seconds": t_gpu,
+                          "oracle_seconds": t_ref, "oracle_cores": os.cpu_count(), "identical_to_oracle": same}),
+              flush=True)
+        return
     if args.min_k:
         pr.min_connected_k(args.min_k)                      # warm-up
         torch.cuda.synchronize()

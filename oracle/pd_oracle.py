@@ -52,6 +52,8 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 __all__ = [
+    "principal_axes",
+    "project_path",
     "geo_distance",
     "knn_composite_weights",
     "min_connected_k",
@@ -461,3 +463,28 @@ def knn_composite_weights(X, mask, coords, alpha: float, k: int, phi, normalize:
         w = np.exp(-phi * d2)
     keep = w > 0.0
     return ei[keep], ej[keep], w[keep], d2[keep], phi
+
+
+def principal_axes(X, mask, q: int):
+    """Leading q principal axes of Y_0 (rows are cases, missing entries at the
+    observed column means; Evaluation of Clusters: the path is displayed on
+    principal components of the original data), as a q x p array of unit rows
+    from the SVD of the column-centred Y_0, with their variances (squared
+    singular values / n).  Sign rule: the entry of largest magnitude of each
+    axis is positive (the first such entry on ties).
+    """
+    Y = fill_missing(X, mask)
+    Yc = Y - Y.mean(axis=0)
+    _, s, Vt = np.linalg.svd(Yc, full_matrices=False)
+    A = Vt[:q].copy()
+    for c in range(A.shape[0]):
+        j = int(np.argmax(np.abs(A[c])))
+        if A[c, j] < 0:
+            A[c] = -A[c]
+    return A, (s[:q] ** 2) / Y.shape[0]
+
+
+def project_path(U, X, mask, axes):
+    """Scores of centroids U (n x p) on the axes: (U - column mean of Y_0) axes^T."""
+    Y = fill_missing(X, mask)
+    return (np.asarray(U, dtype=np.float64) - Y.mean(axis=0)) @ np.asarray(axes).T

@@ -393,3 +393,30 @@ def test_composite_weights_special_cases():
         ei, ej, w, d2, _ = O.knn_composite_weights(Xs, None, cs, 0.0, 1, 0.0, False, geodesic)
         assert list(zip(ei.tolist(), ej.tolist())) == [(0, 1), (2, 3)]
         assert np.allclose(d2, [4.0, 100.0], rtol=1e-12)
+
+
+def test_principal_axes_closed_forms():
+    rng = np.random.default_rng(12)
+    # rank one around a mean: the only axis is the direction b, its variance var(t) |b|^2
+    b = np.array([3.0, -4.0, 0.0, 12.0])
+    t = rng.normal(size=200)
+    X = 5.0 + np.outer(t, b)
+    A, var = O.principal_axes(X, None, 1)
+    assert np.allclose(A[0], b / np.linalg.norm(b) * np.sign(b[np.argmax(np.abs(b))]), atol=1e-12)
+    assert var[0] == pytest.approx(np.var(t) * b @ b, rel=1e-10)
+    # independent coordinates with variances 9, 4, 1 along known orthonormal directions
+    Q, _ = np.linalg.qr(rng.normal(size=(5, 5)))
+    N = 500
+    R = rng.normal(size=(N, 3))
+    R -= R.mean(axis=0)
+    Qz, _ = np.linalg.qr(R)                       # centred orthonormal columns (they stay centred)
+    Z = np.sqrt(N) * Qz * [3.0, 2.0, 1.0]         # covariance exactly diag(9, 4, 1)
+    X = Z @ Q[:3] + 1.0
+    A, var = O.principal_axes(X, None, 3)
+    assert np.allclose(var, [9.0, 4.0, 1.0], rtol=1e-8)
+    for c in range(3):
+        assert abs(abs(A[c] @ Q[c]) - 1.0) < 1e-8
+        assert A[c, np.argmax(np.abs(A[c]))] > 0
+    # scores: the centred data itself projects to its coordinates along the axes
+    S = O.project_path(X, X, None, A)
+    assert np.allclose(np.abs(S), np.abs(Z @ np.eye(3)), atol=1e-7)
