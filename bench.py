@@ -341,6 +341,9 @@ def main():
                     help="instead of the default step: time the kNN weights on the composite distance "
                          "ALPHA * genetic + (1 - ALPHA) * great-circle distance (sampling sites synthetic: one "
                          "site per population plus 2-degree jitter), on the GPU and with the oracle")
+    ap.add_argument("--pc", type=int, default=0, metavar="Q",
+                    help="instead of the default step: time the Q principal axes of the workload on the GPU and "
+                         "with the oracle, and the projected path against the full path through host buffers")
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -395,6 +398,37 @@ def main():
         print(json.dumps({"metric": "seconds per composite-distance kNN weight build", "workload": W["desc"],
                           "alpha": args.composite, "edges": int(ei.size), "gpu_seconds": t_gpu,
                           "oracle_seconds": t_ref, "oracle_cores": os.cpu_count(), "identical_to_oracle": same}),
+              flush=True)
+        return
+    if args.pc:
+        pr.principal_axes(args.pc)                          # warm-up (and cached on the problem)
+        q2 = 1 if args.pc > 1 else 2
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        axes, var = pr.principal_axes(q2)                   # a different q forces a recomputation
+        axes, var = pr.principal_axes(args.pc)
+        torch.cuda.synchronize()
+        t_gpu = (time.perf_counter() - t0) / 2.0
+        import oracle as O
+        t0 = time.perf_counter()
+        oaxes, ovar = O.principal_axes(W["X"].astype(np.float64), W["mask"], args.pc)
+        t_ref = time.perf_counter() - t0
+        sub = gammas[::10]
+        pr.reset_path()
+        t0 = time.perf_counter()
+        pr.solve_path(sub)
+        t_full = time.perf_counter() - t0
+        pr.reset_path()
+        t0 = time.perf_counter()
+        pr.solve_path_projected(sub, args.pc)
+        t_proj = time.perf_counter() - t0
+        print(json.dumps({"metric": "principal axes and projected path", "workload": W["desc"], "q": args.pc,
+                          "axes_gpu_seconds": t_gpu, "axes_oracle_seconds": t_ref,
+                          "max_abs_axis_diff": float(np.abs(axes - oaxes).max()),
+                          "max_rel_var_diff": float(np.max(np.abs(var - ovar) / ovar)),
+                          "path_gammas": len(sub), "path_host_outputs_seconds": t_full,
+                          "path_projected_seconds": t_proj,
+                          "bytes_out_per_gamma_full": int(n * p * 4), "bytes_out_per_gamma_projected": int(n * args.pc * 4)}),
               flush=True)
         return
     if args.min_k:

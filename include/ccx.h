@@ -266,6 +266,32 @@ ccx_status ccx_wait(ccx_server* srv, uint64_t ticket, int64_t timeout_ms);
 ccx_status ccx_server_destroy(ccx_server* srv);
 
 /*
+ * Leading principal axes of the data (Evaluation of Clusters: the path is
+ * displayed on principal components of the original data).  Y_0 (missing
+ * entries at observed column means) is centred by its column means; the axes
+ * are its leading q right singular vectors, computed on the GPU by subspace
+ * iteration with q + 8 vectors and a Rayleigh-Ritz step in double, each signed
+ * so that its entry of largest magnitude is positive.
+ *   q        : 1 <= q <= 8 and q <= min(n, p).
+ *   axes_out : NULL, or host q x p doubles (row c = axis c).
+ *   var_out  : NULL, or host q doubles: variance of the data along each axis.
+ * The axes are kept with the problem for ccx_solve_path_projected.
+ */
+ccx_status ccx_principal_axes(ccx_problem* pr, int q, double* axes_out, double* var_out);
+
+/*
+ * ccx_solve_path, but each gamma's centroids are projected on the GPU onto
+ * the q principal axes above before they leave the device:
+ *   scores_out : NULL, or n_gamma x n x q floats, host or device; entry
+ *                (g, i, c) = <u_i(gamma_g) - mean of Y_0, axis c>.
+ * The paper names the per-gamma transfer of U as its GPU bottleneck; this
+ * moves n q instead of n p values per gamma.  Other arguments as in
+ * ccx_solve_path (the path continues from the problem's warm-start state).
+ */
+ccx_status ccx_solve_path_projected(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts, int q,
+                                    float* scores_out, int32_t* labels_out, ccx_gamma_stats* stats);
+
+/*
  * Solve the paths of several independent problems together (each as
  * ccx_solve_path would, from its own warm-start state; the paper treats one
  * problem at a time, so this adds scheduling only).  Problem i runs its own

@@ -55,6 +55,8 @@ _sigs = {
     "ccx_get_edges": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P]),
     "ccx_min_connected_k": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "ccx_build_knn_composite": (C.c_int, [_P, C.POINTER(KnnRule), _P, C.c_double, C.c_int]),
+    "ccx_principal_axes": (C.c_int, [_P, C.c_int, _P, _P]),
+    "ccx_solve_path_projected": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), C.c_int, _P, _P, _P]),
     "ccx_fusion_scale": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_fusion_scale_noalloc": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
@@ -160,6 +162,34 @@ def build_knn_composite(h, k: int, coords, alpha: float, phi: float = 0.0, phi_a
     r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)))
     c = np.ascontiguousarray(coords, dtype=np.float64)
     _check(_lib.ccx_build_knn_composite(h, C.byref(r), c.ctypes.data, float(alpha), int(bool(geodesic))))
+
+
+def principal_axes(h, q: int, p: int):
+    """(axes q x p, variances q) of the column-centred Y_0."""
+    axes = np.zeros((q, p), np.float64)
+    var = np.zeros(q, np.float64)
+    _check(_lib.ccx_principal_axes(h, int(q), axes.ctypes.data, var.ctypes.data))
+    return axes, var
+
+
+def solve_path_projected(h, gammas, n: int, q: int, opts: Opts | None = None, device: bool = False):
+    """Path with each gamma's centroids projected on the q principal axes on the GPU.
+    Returns (scores (G x n x q float32), labels (G x n int32), stats list, status)."""
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    G = g.size
+    if device:
+        import torch
+        S = torch.empty((G, n, q), dtype=torch.float32, device="cuda")
+        L = torch.empty((G, n), dtype=torch.int32, device="cuda")
+        sp, lp = S.data_ptr(), L.data_ptr()
+    else:
+        S = np.empty((G, n, q), np.float32)
+        L = np.empty((G, n), np.int32)
+        sp, lp = S.ctypes.data, L.ctypes.data
+    stats = (GammaStats * max(G, 1))()
+    o = C.byref(opts) if opts is not None else None
+    st = _check(_lib.ccx_solve_path_projected(h, g.ctypes.data, G, o, int(q), sp, lp, stats), allow=(0, 4))
+    return S, L, [stats[k].as_dict() for k in range(G)], st
 
 
 def min_connected_k(h, k_max: int) -> int:
@@ -347,6 +377,12 @@ class Problem:
 
     def min_connected_k(self, k_max):
         return min_connected_k(self.h, k_max)
+
+    def principal_axes(self, q):
+        return principal_axes(self.h, q, self.p)
+
+    def solve_path_projected(self, gammas, q, opts=None, device=False):
+        return solve_path_projected(self.h, gammas, self.n, q, opts, device)
 
     def build_knn_composite(self, k, coords, alpha, phi=0.0, phi_auto=False, normalize=False, geodesic=False):
         build_knn_composite(self.h, k, coords, alpha, phi, phi_auto, normalize, geodesic)

@@ -135,6 +135,10 @@ struct ccx_problem {
     int* cc_scratch = nullptr;
     int* d_ncl = nullptr;
     int* h_ncl = nullptr;        // pinned
+    double* pc_axes = nullptr;   // q x p principal axes of Y_0 (device), computed on request
+    int pc_q = 0;
+    std::vector<double> pc_var;
+    float* Sstage = nullptr;     // n x q projected scores (device staging for host outputs)
     bool path_ready = false;
     bool path_started = false;
     cudaGraphExec_t graph = nullptr;
@@ -213,6 +217,8 @@ void free_all(ccx_problem* pr) {
     cudaFree(pr->maskbits);
     cudaFree(pr->colmean);
     cudaFree(pr->Y0f);
+    cudaFree(pr->pc_axes);
+    cudaFree(pr->Sstage);
     cudaFree(pr->Y0d);
     cudaFree(pr->d_ss);
     if (pr->ev_user) cudaEventDestroy(pr->ev_user);
@@ -602,7 +608,9 @@ struct PathRun {
     float* U_out = nullptr;
     int32_t* labels_out = nullptr;
     ccx_gamma_stats* stats = nullptr;
-    bool u_dev = false, l_dev = false;
+    int pc_q = 0;                  // > 0: write the scores on the principal axes instead of U
+    float* scores_out = nullptr;
+    bool u_dev = false, l_dev = false, s_dev = false;
     enum Phase { kIterate, kOutputs, kDone } phase = kDone;
     int g = 0, launched = 0, checked = 0;
     double rho = 0.0, eps = 0.0;
@@ -654,6 +662,7 @@ ccx_status path_open(PathRun& r) {
     if (s != CCX_OK) return s;
     r.u_dev = is_device_ptr(r.U_out);
     r.l_dev = is_device_ptr(r.labels_out);
+    r.s_dev = is_device_ptr(r.scores_out);
     r.g = 0;
     r.all_conv = true;
     r.phase = PathRun::kDone;
@@ -704,6 +713,17 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
                 CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(float) * pr->ld_in, pr->Ustage, sizeof(float) * pr->p,
                                            sizeof(float) * pr->p, pr->n, cudaMemcpyDeviceToHost, pr->work));
             }
+        }
+        if (r.pc_q > 0 && r.scores_out) {
+            // project on the GPU: only n x q scores leave the device
+            CUDA_TRY(launch_pd_finalize<R>(P, pr->Ustage, pr->p, (int)pr->p, pr->work));
+            const size_t nq = (size_t)pr->n * r.pc_q;
+            float* sdst = r.s_dev ? r.scores_out + (size_t)g * nq : pr->Sstage;
+            CUDA_TRY(pc_project(pr->Ustage, (int)pr->p, pr->colmean, pr->pc_axes, (int)pr->n, (int)pr->p, r.pc_q,
+                                sdst, pr->work));
+            if (!r.s_dev)
+                CUDA_TRY(cudaMemcpyAsync(r.scores_out + (size_t)g * nq, pr->Sstage, sizeof(float) * nq,
+                                         cudaMemcpyDeviceToHost, pr->work));
         }
         int* ldst = (r.labels_out && r.l_dev) ? r.labels_out + (size_t)g * pr->n : pr->Lstage;
         CUDA_TRY(launch_fused_labels((int)pr->n, P.m, pr->d_ei, pr->d_ej, pr->fused, ldst, pr->d_ncl,
@@ -1072,6 +1092,71 @@ ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, co
     r.gammas = gammas;
     r.n_gamma = n_gamma;
     r.U_out = U_out;
+    r.labels_out = labels_out;
+    r.stats = stats;
+    s = path_open_any(r);
+    if (s != CCX_OK) return s;
+    while (s == CCX_OK && r.phase != PathRun::kDone) {
+        bool progressed = false;
+        s = path_step_any(r, true, &progressed);
+    }
+    return path_close(r, s);
+}
+
+namespace {
+// principal axes cached on the problem (recomputed when q changes)
+ccx_status ensure_axes(ccx_problem* pr, int q) {
+    if (q < 1 || q > pc_max_axes()) return fail(CCX_EINVAL, "q must be in [1, %d]", pc_max_axes());
+    if (q > std::min<int64_t>(pr->n, pr->p)) return fail(CCX_EINVAL, "q must be <= min(n, p)");
+    if (pr->pc_axes && pr->pc_q == q) return CCX_OK;
+    cudaFree(pr->pc_axes);
+    cudaFree(pr->Sstage);
+    pr->pc_axes = nullptr;
+    pr->Sstage = nullptr;
+    pr->pc_q = 0;
+    CUDA_TRY(dalloc(&pr->pc_axes, (size_t)q * pr->p));
+    CUDA_TRY(dalloc(&pr->Sstage, (size_t)q * pr->n));
+    pr->pc_var.assign(q, 0.0);
+    CUDA_TRY(pc_axes(pr->Y0f, pr->colmean, (int)pr->n, (int)pr->p, pr->ld, q, pr->pc_axes, pr->pc_var.data(),
+                     pr->work));
+    pr->pc_q = q;
+    return CCX_OK;
+}
+}  // namespace
+
+ccx_status ccx_principal_axes(ccx_problem* pr, int q, double* axes_out, double* var_out) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    s = ensure_axes(pr, q);
+    if (s != CCX_OK) return s;
+    if (axes_out)
+        CUDA_TRY(cudaMemcpyAsync(axes_out, pr->pc_axes, sizeof(double) * (size_t)q * pr->p, cudaMemcpyDeviceToHost,
+                                 pr->work));
+    if (var_out) std::copy(pr->pc_var.begin(), pr->pc_var.end(), var_out);
+    return leave(pr);
+}
+
+ccx_status ccx_solve_path_projected(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts, int q,
+                                    float* scores_out, int32_t* labels_out, ccx_gamma_stats* stats) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    ccx_status s = check_gammas(gammas, n_gamma);
+    if (s != CCX_OK) return s;
+    PathRun r;
+    s = resolve_opts(pr, opts, &r.o);
+    if (s != CCX_OK) return s;
+    s = enter(pr);
+    if (s != CCX_OK) return s;
+    s = ensure_axes(pr, q);
+    if (s != CCX_OK) return s;
+    pr->stream_edges = r.o.stream_edges ? 1 : 0;
+    r.pr = pr;
+    r.gammas = gammas;
+    r.n_gamma = n_gamma;
+    r.pc_q = q;
+    r.scores_out = scores_out;
     r.labels_out = labels_out;
     r.stats = stats;
     s = path_open_any(r);

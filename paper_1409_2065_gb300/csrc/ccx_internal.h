@@ -169,6 +169,14 @@ struct KnnResult {
 cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
                       cudaStream_t s, KnnResult* out, std::string* err, const double* geo = nullptr,
                       double alpha = 1.0, int geodesic = 0);
+// principal axes of Y_0 (pc_kernels.cu): axes q x p doubles (device), variances on the host
+int pc_max_axes();
+cudaError_t pc_axes(const float* Y0f, const double* mean, int n, int p, int ld, int q, double* axes, double* var_h,
+                    cudaStream_t s);
+// S (n x q floats, device) = (U - mean) axes^T for U n x ldu floats (device)
+cudaError_t pc_project(const float* U, int ldu, const double* mean, const double* axes, int n, int p, int q, float* S,
+                       cudaStream_t s);
+
 // smallest k in [1, k_max] whose kNN union graph is connected (0: none), by
 // bisection over GPU connected components of the k-prefix of the neighbour lists
 cudaError_t knn_min_connected_k(const float* Y0f, int n, int p, int ld, int k_max, cudaStream_t s, int* k_out,

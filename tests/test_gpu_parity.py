@@ -203,6 +203,45 @@ def test_knn_composite_matches_oracle(ccx, alpha, geodesic, frac):
     assert np.allclose(w, ow, rtol=1e-10, atol=0)
 
 
+def _spectrum_data(n, p, seed):
+    """Data with a well separated spectrum: independent scores along orthonormal directions with
+    standard deviations 10, 6, 3.5, 2, then an isotropic unit background."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.normal(size=(p, 4)))
+    Z = rng.normal(size=(n, 4)) * [10.0, 6.0, 3.5, 2.0]
+    return (Z @ Q.T + rng.normal(size=(n, p)) + 2.0).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,p,q,frac", [(400, 300, 3, 0.0), (250, 1000, 2, 0.05)])
+def test_principal_axes_match_oracle(ccx, n, p, q, frac):
+    X = _spectrum_data(n, p, n + p)
+    mask = synth.random_mask(np.random.default_rng(7), n, p, frac) if frac > 0 else None
+    pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+    axes, var = pr.principal_axes(q)
+    oaxes, ovar = O.principal_axes(X.astype(np.float64), mask, q)
+    assert np.allclose(var, ovar, rtol=1e-5)
+    assert np.abs(axes - oaxes).max() <= 1e-5
+    assert np.allclose(axes @ axes.T, np.eye(q), atol=1e-10)
+
+
+def test_projected_path_matches_projection_of_U(ccx):
+    """Scores written on the GPU equal the oracle's projection of the same path's centroids."""
+    X = _spectrum_data(200, 60, 3)
+    pr = ccx.Problem(X, None, ccx.CCX_FP32)
+    pr.build_knn(8, phi_auto=True, normalize=True)
+    g0 = pr.fusion_scale()
+    gam = synth.log_grid(0.05 * g0, 2.0 * g0, 4)
+    U, L, _, _ = pr.solve_path(gam)
+    pr.reset_path()
+    S, L2, stats, st = pr.solve_path_projected(gam, 2)
+    Sd, L3, _, _ = (pr.reset_path(), pr.solve_path_projected(gam, 2, device=True))[1]
+    axes, _ = O.principal_axes(X.astype(np.float64), None, 2)
+    for g in range(len(gam)):
+        ref = O.project_path(U[g], X.astype(np.float64), None, axes)
+        assert np.abs(S[g] - ref).max() <= 1e-4 * np.abs(ref).max()
+    assert np.array_equal(L2, L) and np.array_equal(S, Sd.cpu().numpy())
+
+
 def test_knn_all_pairs(ccx):
     X, _ = synth.expression_like(20, 300, 3, 40, seed=2)
     pr = ccx.Problem(X, None, ccx.CCX_FP32)
