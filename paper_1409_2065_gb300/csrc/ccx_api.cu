@@ -392,8 +392,9 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
     const int64_t m2 = 2 * (int64_t)m;
     const int la = (int)std::max<int64_t>(1, (m2 + T - 1) / T);
     const int le = std::max(1, (m + T - 1) / T);
-    // bank groups of a node's 16-byte shared rows: 8 for float rows (16 bytes), 4 for double rows
-    const int ncol = pr->precision == CCX_FP64 ? 4 : 8;
+    // bank groups of a node's shared row slice: 128 bytes / row bytes (8 for 16-byte rows, 4 for 32-byte)
+    const int row_bytes = kSliceCols * (pr->precision == CCX_FP64 ? 8 : 4);
+    const int ncol = std::max(1, 128 / std::max(16, row_bytes));
     std::vector<int> csr_val(csr.begin(), csr.end());
     const std::vector<int64_t> atA = arrange_runs(T, la, m2, csr_val, rowof, ncol);
     const std::vector<int64_t> atE = arrange_runs(T, le, m, pr->ej, pr->ei, ncol);

@@ -52,6 +52,7 @@ struct alignas(sizeof(R) * C) Vec {
 };
 
 constexpr int C = kSliceCols;
+constexpr uint32_t kSliceMask = (C >= 32) ? 0xFFFFFFFFu : ((1u << C) - 1u);   // mask bits of one slice
 
 __device__ __forceinline__ void ff_add(float hi, float lo, float inc, float& ohi, float& olo) {
     // (hi, lo) + inc in float-float: two-sum of hi and inc, then renormalise.
@@ -350,11 +351,11 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         V qv0, qv1, ev0, ev1;
         if (maskg) {
             const int i0 = tid, i1 = tid + kSliceThreads;
-            if (i0 < n && ((sM[i0] >> (c0 & 31)) & 0xFu) != 0xFu) {
+            if (i0 < n && ((sM[i0] >> (c0 & 31)) & kSliceMask) != kSliceMask) {
                 qv0 = *reinterpret_cast<const V*>(P.Q + (size_t)i0 * ld + c0);
                 ev0 = *reinterpret_cast<const V*>(P.Em + (size_t)i0 * ld + c0);
             }
-            if (i1 < n && ((sM[i1] >> (c0 & 31)) & 0xFu) != 0xFu) {
+            if (i1 < n && ((sM[i1] >> (c0 & 31)) & kSliceMask) != kSliceMask) {
                 qv1 = *reinterpret_cast<const V*>(P.Q + (size_t)i1 * ld + c0);
                 ev1 = *reinterpret_cast<const V*>(P.Em + (size_t)i1 * ld + c0);
             }
@@ -362,9 +363,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
         for (int i = tid, u = 0; i < n; i += kSliceThreads, ++u) {
             const size_t off = (size_t)i * ld + c0;
             const V x = sX[i];
-            const uint32_t obs = maskg ? (sM[i] >> (c0 & 31)) & 0xFu : 0xFu;
+            const uint32_t obs = maskg ? (sM[i] >> (c0 & 31)) & kSliceMask : kSliceMask;
             V qv, ev;
-            if (obs != 0xFu) {
+            if (obs != kSliceMask) {
                 if (u == 0) {
                     qv = qv0;
                     ev = ev0;
