@@ -86,6 +86,10 @@ typedef struct {
     int max_iter;      /* MM iterations per gamma; default 200000 */
     int accelerate;    /* 1: Nesterov-extrapolated MM with restarts (default); 0: the plain MM iteration */
     int chunk;         /* iterations per captured CUDA graph launch; default 64 */
+    int extrapolate;   /* 1 (default): from the third gamma of a call on, start each gamma from the
+                          secant prediction A_k + c (A_k - A_(k-1)) of the last two solutions
+                          (c from the log-gamma spacing, at most 1); 0: start from A_k.  The fixed
+                          point is the same either way. */
     int stream_edges;  /* 0 (default): the iteration kernel keeps the per-edge index and accumulator
                           arrays in shared memory when they fit beside the rows of a slice, and in
                           global memory otherwise; 1: always in global memory.  Results are

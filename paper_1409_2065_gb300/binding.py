@@ -34,7 +34,8 @@ class KnnRule(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("rho_scale", C.c_double), ("eps_rel", C.c_double), ("tol", C.c_double),
-                ("max_iter", C.c_int), ("accelerate", C.c_int), ("chunk", C.c_int), ("stream_edges", C.c_int)]
+                ("max_iter", C.c_int), ("accelerate", C.c_int), ("chunk", C.c_int), ("extrapolate", C.c_int),
+                ("stream_edges", C.c_int)]
 
 
 class GammaStats(C.Structure):

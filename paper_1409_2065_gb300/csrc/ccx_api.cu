@@ -139,6 +139,8 @@ struct ccx_problem {
     int pc_q = 0;
     std::vector<double> pc_var;
     float* Sstage = nullptr;     // n x q projected scores (device staging for host outputs)
+    void* Aprev = nullptr;       // A at the end of the previous gamma (hi, or double)
+    float* Aprev_lo = nullptr;   // its lo part (FP32 path)
     bool path_ready = false;
     bool path_started = false;
     cudaGraphExec_t graph = nullptr;
@@ -160,6 +162,10 @@ void free_path(ccx_problem* pr) {
     }
     cudaFree(pr->Q);
     cudaFree(pr->Em);
+    cudaFree(pr->Aprev);
+    cudaFree(pr->Aprev_lo);
+    pr->Aprev = nullptr;
+    pr->Aprev_lo = nullptr;
     cudaFree(pr->Pnb);
     cudaFree(pr->Ps);
     cudaFree(pr->nb);
@@ -542,6 +548,10 @@ ccx_status ensure_path(ccx_problem* pr) {
         CUDA_TRY(cudaMalloc(&pr->A[k], es * nl));
         CUDA_TRY(cudaMalloc(&pr->Dl[k], es * nl));
         if (!fp64) CUDA_TRY(dalloc(&pr->Alo[k], nl));
+        if (k == 0) {
+            CUDA_TRY(cudaMalloc(&pr->Aprev, es * nl));
+            if (!fp64) CUDA_TRY(dalloc(&pr->Aprev_lo, nl));
+        }
         // a (t, t_prev) pair per node-sweep and per edge-sweep position
         CUDA_TRY(cudaMalloc(&pr->t[k], es * 2 * ((size_t)pr->la + pr->le) * kSliceThreads));
     }
@@ -631,6 +641,20 @@ ccx_status path_begin_gamma(PathRun& r) {
     const double unit = std::is_same<R, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     const double scale_floor = 64.0 * unit * pr->ny0;
     r.t0 = std::chrono::steady_clock::now();
+    if (r.o.extrapolate && r.g >= 1) {
+        // secant step along the path in log gamma (c = 0 on the second gamma: A is only recorded)
+        double c = 0.0;
+        if (r.g >= 2) {
+            const double g0 = r.gammas[r.g - 2], g1 = r.gammas[r.g - 1];
+            if (g0 > 0.0 && g1 > 0.0 && gamma > 0.0 && g1 != g0) {
+                c = std::log(gamma / g1) / std::log(g1 / g0);
+                if (!(c > 0.0)) c = 0.0;
+                c = std::min(c, 1.0);
+            }
+        }
+        CUDA_TRY(launch_pd_extrapolate<R>(make_params<R>(pr), reinterpret_cast<R*>(pr->Aprev), pr->Aprev_lo, c,
+                                          pr->work));
+    }
     CUDA_TRY(launch_pd_begin_gamma<R>(make_params<R>(pr), gamma, r.rho, r.eps, r.o.tol, r.o.max_iter,
                                       r.o.accelerate, scale_floor, pr->work));
     r.launched = r.checked = 0;
@@ -821,6 +845,7 @@ void ccx_opts_default(ccx_opts* o) {
     o->max_iter = 200000;
     o->accelerate = 1;
     o->chunk = 64;
+    o->extrapolate = 1;
     o->stream_edges = 0;
 }
 
@@ -1263,7 +1288,7 @@ size_t path_bytes(const ccx_problem* pr) {
     const size_t nsl = (size_t)((pr->p + kSliceCols - 1) / kSliceCols);
     const size_t G = std::min<size_t>(nsl, (size_t)std::max(pr->num_sms, 1));
     const size_t T = kSliceThreads;
-    size_t b = 4 * es * nl + (fp64 ? 0 : 2 * 4 * nl) + (pr->has_mask ? 2 * es * nl : 0);
+    size_t b = 5 * es * nl + (fp64 ? 0 : 3 * 4 * nl) + (pr->has_mask ? 2 * es * nl : 0);
     b += 2 * es * 2 * ((size_t)pr->la + pr->le) * T;
     b += G * (size_t)pr->le * T * 4 + G * 64 + m * 9 + 16 * (size_t)pd_reduce_blocks(pr->le);
     b += (size_t)pr->n * pr->p * 4 + (size_t)pr->n * 8 + 4096;
