@@ -336,6 +336,24 @@ ccx_status ccx_problem_destroy(ccx_problem* pr);
 ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts, double* slice_ms,
                                double* reduce_ms);
 
+/*
+ * Instrumentation (no counterpart in the paper; host only, needs no GPU): the
+ * work layout the iteration kernel uses for a sorted edge set (0 <= ei < ej <
+ * n, ordered by (ei, ej), no duplicates; n <= 65535).  The kernel's T threads
+ * each walk a run of la node-sweep entries (CSR entries over both directions,
+ * row by row) and a run of le edge-sweep entries (edge ids in order); entry k
+ * of run t sits at position k * T + t, and inside each row of a run the order
+ * is chosen against shared-memory bank conflicts.
+ *   sizes    : 4 ints out: T, la, le, number of node-sweep partial slots.
+ *   node_row, node_nbr : NULL, or la * T ints: row (case) and neighbour of
+ *              each node-sweep position, -1 past the end of a run.
+ *   edge_id  : NULL, or le * T ints: edge index of each edge-sweep position,
+ *              -1 past the end.
+ * Call once with NULL arrays to learn the sizes.  CCX_EINVAL on bad input.
+ */
+ccx_status ccx_sweep_plan(int64_t n, int64_t n_edges, const int32_t* ei, const int32_t* ej, int precision,
+                          int32_t* sizes, int32_t* node_row, int32_t* node_nbr, int32_t* edge_id);
+
 /* Number of GPU kernels this library has launched in the process so far
  * (all problems; kernels inside CUDA-graph launches are counted). */
 uint64_t ccx_kernel_launches(void);

@@ -71,6 +71,7 @@ _sigs = {
     "ccx_time_iterations": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]),
     "ccx_kernel_launches": (C.c_uint64, []),
+    "ccx_sweep_plan": (C.c_int, [C.c_int64, C.c_int64, _P, _P, C.c_int, _P, _P, _P, _P]),
     "ccx_last_error": (C.c_char_p, []),
     "ccx_version": (C.c_char_p, []),
 }
@@ -354,6 +355,23 @@ def time_iterations(h, gamma: float, n_iter: int, opts: Opts | None = None):
     o = C.byref(opts) if opts is not None else None
     _check(_lib.ccx_time_iterations(h, float(gamma), int(n_iter), o, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def sweep_plan(n: int, ei, ej, precision=CCX_FP32):
+    """Work layout of the iteration kernel (host only): (T, la, le, nslots, node_row, node_nbr, edge_id),
+    the arrays indexed by position k * T + t (-1 past the end of a run)."""
+    ei = np.ascontiguousarray(ei, dtype=np.int32)
+    ej = np.ascontiguousarray(ej, dtype=np.int32)
+    sz = np.zeros(4, np.int32)
+    _check(_lib.ccx_sweep_plan(int(n), ei.size, ei.ctypes.data, ej.ctypes.data, int(precision), sz.ctypes.data,
+                               None, None, None))
+    T, la, le, ns = (int(v) for v in sz)
+    row = np.empty(la * T, np.int32)
+    nbr = np.empty(la * T, np.int32)
+    eid = np.empty(le * T, np.int32)
+    _check(_lib.ccx_sweep_plan(int(n), ei.size, ei.ctypes.data, ej.ctypes.data, int(precision), sz.ctypes.data,
+                               row.ctypes.data, nbr.ctypes.data, eid.ctypes.data))
+    return T, la, le, ns, row, nbr, eid
 
 
 def kernel_launches() -> int:

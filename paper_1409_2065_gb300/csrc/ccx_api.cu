@@ -333,6 +333,111 @@ std::vector<int64_t> arrange_runs(int T, int L, int64_t N, const std::vector<int
     return at;
 }
 
+// The work layout of the iteration kernel's two sweeps for a sorted edge set
+// (i < j, ordered by (i, j), no duplicates): CSR over both directions, the
+// equal per-thread runs with their bank-aware order, partial slots and the
+// position maps the reduction uses.  Host only.
+struct SweepPlan {
+    int la = 1, le = 1, nslots = 0, deg_max = 0;
+    std::vector<int> rowptr, erow, ps0, thrE, eid, node_row;
+    std::vector<uint16_t> csrT, ejT;
+    std::vector<uint2> thrA;
+    std::vector<int2> posE;
+};
+
+SweepPlan plan_sweeps(int64_t n, const std::vector<int>& ei, const std::vector<int>& ej, int precision) {
+    SweepPlan P;
+    const int m = (int)ei.size();
+    std::vector<int> deg(n, 0);
+    for (int q = 0; q < m; ++q) {
+        deg[ei[q]]++;
+        deg[ej[q]]++;
+    }
+    std::vector<int> rowptr(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
+    P.deg_max = n > 0 ? *std::max_element(deg.begin(), deg.end()) : 0;
+    std::vector<std::pair<int, int>> ent(2 * (size_t)m);
+    std::vector<int> fillp(rowptr.begin(), rowptr.end() - 1);
+    for (int q = 0; q < m; ++q) {
+        ent[fillp[ei[q]]++] = {ej[q], q};
+        ent[fillp[ej[q]]++] = {ei[q], q};
+    }
+    // rows by increasing neighbour; qa/qb: CSR position of edge e in the row of ei / ej
+    std::vector<uint16_t> csr(2 * (size_t)m);
+    std::vector<int> qa(m), qb(m), rowof(2 * (size_t)m);
+    for (int64_t i = 0; i < n; ++i) {
+        std::sort(ent.begin() + rowptr[i], ent.begin() + rowptr[i + 1]);
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            csr[k] = (uint16_t)ent[k].first;
+            rowof[k] = (int)i;
+            (ent[k].first > i ? qa : qb)[ent[k].second] = k;
+        }
+    }
+    // equal runs of the two sweeps, one per thread of the iteration kernel
+    const int T = kSliceThreads;
+    const int64_t m2 = 2 * (int64_t)m;
+    const int la = (int)std::max<int64_t>(1, (m2 + T - 1) / T);
+    const int le = std::max(1, (m + T - 1) / T);
+    // bank groups of a node's shared row slice: 128 bytes / row bytes (8 for 16-byte rows, 4 for 32-byte)
+    const int row_bytes = kSliceCols * (precision == CCX_FP64 ? 8 : 4);
+    const int ncol = std::max(1, 128 / std::max(16, row_bytes));
+    std::vector<int> csr_val(csr.begin(), csr.end());
+    const std::vector<int64_t> atA = arrange_runs(T, la, m2, csr_val, rowof, ncol);
+    const std::vector<int64_t> atE = arrange_runs(T, le, m, ej, ei, ncol);
+    std::vector<int> posA_of(m2 > 0 ? m2 : 1);
+    std::vector<uint16_t> csrT((size_t)la * T, 0), ejT((size_t)le * T, 0);
+    for (size_t x = 0; x < atA.size(); ++x)
+        if (atA[x] >= 0) {
+            csrT[x] = csr[atA[x]];
+            posA_of[atA[x]] = (int)x;
+        }
+    std::vector<int> eid((size_t)le * T, -1);
+    std::vector<int2> posE((size_t)le * T, make_int2(0, 0));
+    for (size_t x = 0; x < atE.size(); ++x)
+        if (atE[x] >= 0) {
+            const int e = (int)atE[x];
+            ejT[x] = (uint16_t)ej[e];
+            eid[x] = e;
+            posE[x] = make_int2(posA_of[qa[e]], posA_of[qb[e]]);
+        }
+    // node-sweep partial slots: one per (run, row) overlap, numbered in entry
+    // order, so the slots of a node are consecutive
+    std::vector<uint2> thrA(T);
+    std::vector<int> ps0(n + 1, 0);
+    int nslots = 0;
+    for (int t = 0; t < T; ++t) {
+        const int64_t q0 = (int64_t)t * la, q1 = std::min<int64_t>(q0 + la, m2);
+        thrA[t] = make_uint2(q0 < q1 ? (uint32_t)rowof[q0] : 0u, (uint32_t)nslots);
+        for (int64_t q = q0; q < q1; ++q)
+            if (q == q0 || rowof[q] != rowof[q - 1]) {
+                ps0[rowof[q] + 1]++;
+                ++nslots;
+            }
+    }
+    for (int64_t i = 0; i < n; ++i) ps0[i + 1] += ps0[i];
+    std::vector<int> erow(n + 1, 0), thrE(T, 0);
+    for (int e = 0; e < m; ++e) erow[ei[e] + 1]++;
+    for (int64_t i = 0; i < n; ++i) erow[i + 1] += erow[i];
+    for (int t = 0; t < T; ++t)
+        if ((int64_t)t * le < m) thrE[t] = ei[(size_t)t * le];
+    P.node_row.assign((size_t)la * T, -1);
+    for (size_t x = 0; x < atA.size(); ++x)
+        if (atA[x] >= 0) P.node_row[x] = rowof[atA[x]];
+    P.la = la;
+    P.le = le;
+    P.nslots = nslots;
+    P.rowptr = std::move(rowptr);
+    P.erow = std::move(erow);
+    P.ps0 = std::move(ps0);
+    P.thrE = std::move(thrE);
+    P.eid = std::move(eid);
+    P.csrT = std::move(csrT);
+    P.ejT = std::move(ejT);
+    P.thrA = std::move(thrA);
+    P.posE = std::move(posE);
+    return P;
+}
+
 // Validate, sort by (i, j), drop zero weights, store and upload with CSR.
 ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const std::vector<int>& ej_in,
                          const std::vector<double>& w_in) {
@@ -368,78 +473,19 @@ ccx_status install_edges(ccx_problem* pr, const std::vector<int>& ei_in, const s
     }
     pr->nw = std::sqrt(s2);
     // CSR over both directions; each row lists its neighbours by increasing index
-    std::vector<int> deg(n, 0);
-    for (int q = 0; q < m; ++q) {
-        deg[pr->ei[q]]++;
-        deg[pr->ej[q]]++;
-    }
-    std::vector<int> rowptr(n + 1, 0);
-    for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
-    pr->deg_max = n > 0 ? *std::max_element(deg.begin(), deg.end()) : 0;
-    std::vector<std::pair<int, int>> ent(2 * (size_t)m);
-    std::vector<int> fillp(rowptr.begin(), rowptr.end() - 1);
-    for (int q = 0; q < m; ++q) {
-        ent[fillp[pr->ei[q]]++] = {pr->ej[q], q};
-        ent[fillp[pr->ej[q]]++] = {pr->ei[q], q};
-    }
-    // rows by increasing neighbour; qa/qb: CSR position of edge e in the row of ei / ej
-    std::vector<uint16_t> csr(2 * (size_t)m);
-    std::vector<int> qa(m), qb(m), rowof(2 * (size_t)m);
-    for (int64_t i = 0; i < n; ++i) {
-        std::sort(ent.begin() + rowptr[i], ent.begin() + rowptr[i + 1]);
-        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-            csr[k] = (uint16_t)ent[k].first;
-            rowof[k] = (int)i;
-            (ent[k].first > i ? qa : qb)[ent[k].second] = k;
-        }
-    }
-    // equal runs of the two sweeps, one per thread of the iteration kernel
+    SweepPlan P = plan_sweeps(n, pr->ei, pr->ej, pr->precision);
+    pr->deg_max = P.deg_max;
     const int T = kSliceThreads;
-    const int64_t m2 = 2 * (int64_t)m;
-    const int la = (int)std::max<int64_t>(1, (m2 + T - 1) / T);
-    const int le = std::max(1, (m + T - 1) / T);
-    // bank groups of a node's shared row slice: 128 bytes / row bytes (8 for 16-byte rows, 4 for 32-byte)
-    const int row_bytes = kSliceCols * (pr->precision == CCX_FP64 ? 8 : 4);
-    const int ncol = std::max(1, 128 / std::max(16, row_bytes));
-    std::vector<int> csr_val(csr.begin(), csr.end());
-    const std::vector<int64_t> atA = arrange_runs(T, la, m2, csr_val, rowof, ncol);
-    const std::vector<int64_t> atE = arrange_runs(T, le, m, pr->ej, pr->ei, ncol);
-    std::vector<int> posA_of(m2 > 0 ? m2 : 1);
-    std::vector<uint16_t> csrT((size_t)la * T, 0), ejT((size_t)le * T, 0);
-    for (size_t x = 0; x < atA.size(); ++x)
-        if (atA[x] >= 0) {
-            csrT[x] = csr[atA[x]];
-            posA_of[atA[x]] = (int)x;
-        }
-    std::vector<int> eid((size_t)le * T, -1);
-    std::vector<int2> posE((size_t)le * T, make_int2(0, 0));
-    for (size_t x = 0; x < atE.size(); ++x)
-        if (atE[x] >= 0) {
-            const int e = (int)atE[x];
-            ejT[x] = (uint16_t)pr->ej[e];
-            eid[x] = e;
-            posE[x] = make_int2(posA_of[qa[e]], posA_of[qb[e]]);
-        }
-    // node-sweep partial slots: one per (run, row) overlap, numbered in entry
-    // order, so the slots of a node are consecutive
-    std::vector<uint2> thrA(T);
-    std::vector<int> ps0(n + 1, 0);
-    int nslots = 0;
-    for (int t = 0; t < T; ++t) {
-        const int64_t q0 = (int64_t)t * la, q1 = std::min<int64_t>(q0 + la, m2);
-        thrA[t] = make_uint2(q0 < q1 ? (uint32_t)rowof[q0] : 0u, (uint32_t)nslots);
-        for (int64_t q = q0; q < q1; ++q)
-            if (q == q0 || rowof[q] != rowof[q - 1]) {
-                ps0[rowof[q] + 1]++;
-                ++nslots;
-            }
-    }
-    for (int64_t i = 0; i < n; ++i) ps0[i + 1] += ps0[i];
-    std::vector<int> erow(n + 1, 0), thrE(T, 0);
-    for (int e = 0; e < m; ++e) erow[pr->ei[e] + 1]++;
-    for (int64_t i = 0; i < n; ++i) erow[i + 1] += erow[i];
-    for (int t = 0; t < T; ++t)
-        if ((int64_t)t * le < m) thrE[t] = pr->ei[(size_t)t * le];
+    const int la = P.la, le = P.le, nslots = P.nslots;
+    std::vector<int>& rowptr = P.rowptr;
+    std::vector<int>& erow = P.erow;
+    std::vector<int>& ps0 = P.ps0;
+    std::vector<int>& thrE = P.thrE;
+    std::vector<int>& eid = P.eid;
+    std::vector<uint16_t>& csrT = P.csrT;
+    std::vector<uint16_t>& ejT = P.ejT;
+    std::vector<uint2>& thrA = P.thrA;
+    std::vector<int2>& posE = P.posE;
     free_path(pr);
     free_edges(pr);
     pr->la = la;
@@ -1014,6 +1060,39 @@ ccx_status ccx_build_knn_composite(ccx_problem* pr, const ccx_knn_rule* rule, co
     s = install_edges(pr, res.ei, res.ej, res.w);
     if (s != CCX_OK) return s;
     return leave(pr);
+}
+
+ccx_status ccx_sweep_plan(int64_t n, int64_t n_edges, const int32_t* ei, const int32_t* ej, int precision,
+                          int32_t* sizes, int32_t* node_row, int32_t* node_nbr, int32_t* edge_id) {
+    g_err.clear();
+    if (!sizes) return fail(CCX_EINVAL, "sizes is NULL");
+    if (n < 1 || n > 65535) return fail(CCX_EINVAL, "n must be in [1, 65535]");
+    if (n_edges < 0 || n_edges > (int64_t)1 << 30) return fail(CCX_EINVAL, "bad n_edges");
+    if (n_edges > 0 && (!ei || !ej)) return fail(CCX_EINVAL, "ei or ej is NULL");
+    if (precision != CCX_FP32 && precision != CCX_FP64) return fail(CCX_EINVAL, "precision must be 0 or 1");
+    std::vector<int> a(n_edges), b(n_edges);
+    for (int64_t q = 0; q < n_edges; ++q) {
+        a[q] = ei[q];
+        b[q] = ej[q];
+        if (a[q] < 0 || b[q] >= n || a[q] >= b[q])
+            return fail(CCX_EINVAL, "edge %lld: need 0 <= ei < ej < n", (long long)q);
+        if (q > 0 && (a[q] < a[q - 1] || (a[q] == a[q - 1] && b[q] <= b[q - 1])))
+            return fail(CCX_EINVAL, "edges must be sorted by (ei, ej) without duplicates");
+    }
+    const SweepPlan P = plan_sweeps(n, a, b, precision);
+    const int T = kSliceThreads;
+    sizes[0] = T;
+    sizes[1] = P.la;
+    sizes[2] = P.le;
+    sizes[3] = P.nslots;
+    const size_t LA = (size_t)P.la * T, LE = (size_t)P.le * T;
+    for (size_t x = 0; x < LA; ++x) {
+        if (node_row) node_row[x] = P.node_row[x];
+        if (node_nbr) node_nbr[x] = P.node_row[x] >= 0 ? (int32_t)P.csrT[x] : -1;
+    }
+    if (edge_id)
+        for (size_t x = 0; x < LE; ++x) edge_id[x] = P.eid[x];
+    return CCX_OK;
 }
 
 ccx_status ccx_min_connected_k(ccx_problem* pr, int k_max, int* k_out) {
