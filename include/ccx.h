@@ -88,8 +88,10 @@ typedef struct {
     int chunk;         /* iterations per captured CUDA graph launch; default 64 */
     int extrapolate;   /* 1 (default): from the third gamma of a call on, start each gamma from the
                           secant prediction A_k + c (A_k - A_(k-1)) of the last two solutions
-                          (c from the log-gamma spacing, at most 1); 0: start from A_k.  The fixed
-                          point is the same either way. */
+                          (c from the log-gamma spacing, at most 1); 2: the quadratic through
+                          the last three solutions while the last three gammas stopped on the
+                          tolerance, the secant otherwise; 0: start from A_k.  The fixed point is
+                          the same in every case. */
     int stream_edges;  /* 0 (default): the iteration kernel keeps the per-edge index and accumulator
                           arrays in shared memory when they fit beside the rows of a slice, and in
                           global memory otherwise; 1: always in global memory.  Results are

@@ -141,6 +141,8 @@ struct ccx_problem {
     float* Sstage = nullptr;     // n x q projected scores (device staging for host outputs)
     void* Aprev = nullptr;       // A at the end of the previous gamma (hi, or double)
     float* Aprev_lo = nullptr;   // its lo part (FP32 path)
+    void* Aprev2 = nullptr;      // A at the end of the gamma before that (quadratic predictor)
+    float* Aprev2_lo = nullptr;
     bool path_ready = false;
     bool path_started = false;
     cudaGraphExec_t graph = nullptr;
@@ -164,8 +166,10 @@ void free_path(ccx_problem* pr) {
     cudaFree(pr->Em);
     cudaFree(pr->Aprev);
     cudaFree(pr->Aprev_lo);
-    pr->Aprev = nullptr;
-    pr->Aprev_lo = nullptr;
+    cudaFree(pr->Aprev2);
+    cudaFree(pr->Aprev2_lo);
+    pr->Aprev = pr->Aprev2 = nullptr;
+    pr->Aprev_lo = pr->Aprev2_lo = nullptr;
     cudaFree(pr->Pnb);
     cudaFree(pr->Ps);
     cudaFree(pr->nb);
@@ -671,6 +675,7 @@ struct PathRun {
     enum Phase { kIterate, kOutputs, kDone } phase = kDone;
     int g = 0, launched = 0, checked = 0;
     double rho = 0.0, eps = 0.0;
+    int conv_hist[3] = {0, 0, 0};  // converged flags of the last three gammas (newest first)
     PdState final{};
     std::chrono::steady_clock::time_point t0;
     bool all_conv = true;
@@ -688,18 +693,44 @@ ccx_status path_begin_gamma(PathRun& r) {
     const double scale_floor = 64.0 * unit * pr->ny0;
     r.t0 = std::chrono::steady_clock::now();
     if (r.o.extrapolate && r.g >= 1) {
-        // secant step along the path in log gamma (c = 0 on the second gamma: A is only recorded)
-        double c = 0.0;
-        if (r.g >= 2) {
-            const double g0 = r.gammas[r.g - 2], g1 = r.gammas[r.g - 1];
-            if (g0 > 0.0 && g1 > 0.0 && gamma > 0.0 && g1 != g0) {
-                c = std::log(gamma / g1) / std::log(g1 / g0);
+        // predictor along the path in log gamma: on the second gamma A is only
+        // recorded; then a secant step (c = spacing ratio, at most 1); with
+        // extrapolate = 2, from the fourth gamma on, the quadratic through the
+        // last three solutions
+        double w0 = 1.0, w1 = 0.0, w2 = 0.0;
+        const bool quad = r.o.extrapolate >= 2;
+        if (quad && !pr->Aprev2) {
+            const size_t nl = (size_t)pr->n * pr->ld;
+            const size_t es = std::is_same<R, double>::value ? 8 : 4;
+            CUDA_TRY(cudaMalloc(&pr->Aprev2, es * nl));
+            if (!std::is_same<R, double>::value) CUDA_TRY(dalloc(&pr->Aprev2_lo, nl));
+        }
+        auto lg = [&](int k) { return std::log(k == r.g ? gamma : r.gammas[k]); };
+        bool pos = gamma > 0.0;
+        for (int k = std::max(0, r.g - 3); k < r.g; ++k) pos = pos && r.gammas[k] > 0.0;
+        // the quadratic only while the last three gammas stopped on the tolerance: at
+        // the rounding floor the solutions differ by noise, which its weights amplify
+        const bool smooth = r.conv_hist[0] == 1 && r.conv_hist[1] == 1 && r.conv_hist[2] == 1;
+        if (pos && quad && smooth && r.g >= 3) {
+            const double x0 = lg(r.g - 3), x1 = lg(r.g - 2), x2 = lg(r.g - 1), x = lg(r.g);
+            if (x0 != x1 && x1 != x2 && x0 != x2 && (x - x2) <= (x2 - x1) * 1.0000001) {
+                w0 = (x - x1) * (x - x0) / ((x2 - x1) * (x2 - x0));   // weight of A_k
+                w1 = (x - x2) * (x - x0) / ((x1 - x2) * (x1 - x0));   // A_(k-1)
+                w2 = (x - x2) * (x - x1) / ((x0 - x2) * (x0 - x1));   // A_(k-2)
+            }
+        } else if (pos && r.g >= 2) {
+            const double x1 = lg(r.g - 2), x2 = lg(r.g - 1), x = lg(r.g);
+            if (x2 != x1) {
+                double c = (x - x2) / (x2 - x1);
                 if (!(c > 0.0)) c = 0.0;
                 c = std::min(c, 1.0);
+                w0 = 1.0 + c;
+                w1 = -c;
             }
         }
-        CUDA_TRY(launch_pd_extrapolate<R>(make_params<R>(pr), reinterpret_cast<R*>(pr->Aprev), pr->Aprev_lo, c,
-                                          pr->work));
+        CUDA_TRY(launch_pd_extrapolate<R>(make_params<R>(pr), reinterpret_cast<R*>(pr->Aprev), pr->Aprev_lo,
+                                          quad ? reinterpret_cast<R*>(pr->Aprev2) : nullptr,
+                                          quad ? pr->Aprev2_lo : nullptr, w0, w1, w2, pr->work));
     }
     CUDA_TRY(launch_pd_begin_gamma<R>(make_params<R>(pr), gamma, r.rho, r.eps, r.o.tol, r.o.max_iter,
                                       r.o.accelerate, scale_floor, pr->work));
@@ -736,6 +767,7 @@ ccx_status path_open(PathRun& r) {
     r.s_dev = is_device_ptr(r.scores_out);
     r.g = 0;
     r.all_conv = true;
+    r.conv_hist[0] = r.conv_hist[1] = r.conv_hist[2] = 0;
     r.phase = PathRun::kDone;
     if (r.n_gamma > 0) return path_begin_gamma<R>(r);
     return CCX_OK;
@@ -773,6 +805,9 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
         // The chunk queued behind the finished one returns at once; everything
         // below is ordered after it on the work stream.
         if (r.final.converged == 0) r.all_conv = false;
+        r.conv_hist[2] = r.conv_hist[1];
+        r.conv_hist[1] = r.conv_hist[0];
+        r.conv_hist[0] = r.final.converged;
         IterParams<R> P = make_params<R>(pr);
         const int g = r.g;
         if (r.U_out) {

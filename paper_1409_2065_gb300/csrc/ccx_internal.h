@@ -135,7 +135,8 @@ cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s);
 // library-wide count of kernel launches (incremented by every launcher)
 void count_launches(unsigned long long k);
 template <typename R>
-cudaError_t launch_pd_extrapolate(const IterParams<R>& P, R* prev_hi, float* prev_lo, double c, cudaStream_t s);
+cudaError_t launch_pd_extrapolate(const IterParams<R>& P, R* p1_hi, float* p1_lo, R* p2_hi, float* p2_lo, double w0,
+                                  double w1, double w2, cudaStream_t s);
 template <typename R>
 cudaError_t launch_pd_finalize(const IterParams<R>& P, float* U_out, int64_t ld_out, int p, cudaStream_t s);
 size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch, bool stream);

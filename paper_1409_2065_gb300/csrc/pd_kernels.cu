@@ -911,44 +911,59 @@ cudaError_t launch_pd_begin_gamma(const IterParams<R>& P, double gamma, double r
     return cudaGetLastError();
 }
 
-// Secant predictor between gammas: A <- A + c (A - A_prev) in the slot the next
-// iteration reads, and A_prev <- the old A.  With c = 0 it only records A.
+// Predictor between gammas: A <- w0 A + w1 A_prev + w2 A_prev2 in the slot the
+// next iteration reads, then A_prev2 <- A_prev and A_prev <- the old A.  The
+// weights are the Lagrange extrapolation weights (w0 = 1, w1 = w2 = 0 only
+// records A); a buffer whose weight is 0 is not read (it may not exist yet).
 template <typename R>
-__global__ void pd_extrapolate_kernel(IterParams<R> P, R* __restrict__ prev_hi, float* __restrict__ prev_lo,
-                                      double c, size_t total) {
+__global__ void pd_extrapolate_kernel(IterParams<R> P, R* __restrict__ p1_hi, float* __restrict__ p1_lo,
+                                      R* __restrict__ p2_hi, float* __restrict__ p2_lo, double w0, double w1,
+                                      double w2, size_t total) {
     const int par = P.st->par;
     R* hi = P.Ahi[par];
     float* lo = P.Alo[par];
+    const bool use1 = (w1 != 0.0), use2 = (w2 != 0.0);
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
-        // with c = 0 the previous solution is not read (it may not exist yet)
         if constexpr (std::is_same<R, float>::value) {
             const float h0 = hi[k], l0 = lo[k];
-            if (c != 0.0) {
-                const double v = (double)h0 + (double)l0;
-                const double vp = (double)prev_hi[k] + (double)prev_lo[k];
-                const double w = v + c * (v - vp);
+            const float h1 = p1_hi[k], l1 = p1_lo[k];
+            if (use1 || use2) {
+                double w = w0 * ((double)h0 + (double)l0);
+                if (use1) w += w1 * ((double)h1 + (double)l1);
+                if (use2) w += w2 * ((double)p2_hi[k] + (double)p2_lo[k]);
                 const float h = (float)w;
                 hi[k] = h;
                 lo[k] = (float)(w - (double)h);
             }
-            prev_hi[k] = h0;
-            prev_lo[k] = l0;
+            if (p2_hi) {
+                p2_hi[k] = h1;
+                p2_lo[k] = l1;
+            }
+            p1_hi[k] = h0;
+            p1_lo[k] = l0;
         } else {
-            const double v = hi[k];
-            if (c != 0.0) hi[k] = v + c * (v - prev_hi[k]);
-            prev_hi[k] = v;
+            const double v = hi[k], v1 = p1_hi[k];
+            if (use1 || use2) {
+                double w = w0 * v;
+                if (use1) w += w1 * v1;
+                if (use2) w += w2 * p2_hi[k];
+                hi[k] = w;
+            }
+            if (p2_hi) p2_hi[k] = v1;
+            p1_hi[k] = v;
         }
     }
 }
 
 template <typename R>
-cudaError_t launch_pd_extrapolate(const IterParams<R>& P, R* prev_hi, float* prev_lo, double c, cudaStream_t s) {
+cudaError_t launch_pd_extrapolate(const IterParams<R>& P, R* p1_hi, float* p1_lo, R* p2_hi, float* p2_lo, double w0,
+                                  double w1, double w2, cudaStream_t s) {
     const size_t total = (size_t)P.n * P.ld;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     count_launches(1);
-    pd_extrapolate_kernel<R><<<blocks, 256, 0, s>>>(P, prev_hi, prev_lo, c, total);
+    pd_extrapolate_kernel<R><<<blocks, 256, 0, s>>>(P, p1_hi, p1_lo, p2_hi, p2_lo, w0, w1, w2, total);
     return cudaGetLastError();
 }
 
@@ -975,8 +990,10 @@ template cudaError_t launch_pd_begin_gamma<float>(const IterParams<float>&, doub
                                                   double, cudaStream_t);
 template cudaError_t launch_pd_begin_gamma<double>(const IterParams<double>&, double, double, double, double, int, int,
                                                    double, cudaStream_t);
-template cudaError_t launch_pd_extrapolate<float>(const IterParams<float>&, float*, float*, double, cudaStream_t);
-template cudaError_t launch_pd_extrapolate<double>(const IterParams<double>&, double*, float*, double, cudaStream_t);
+template cudaError_t launch_pd_extrapolate<float>(const IterParams<float>&, float*, float*, float*, float*, double,
+                                                  double, double, cudaStream_t);
+template cudaError_t launch_pd_extrapolate<double>(const IterParams<double>&, double*, float*, double*, float*, double,
+                                                   double, double, cudaStream_t);
 template cudaError_t launch_pd_finalize<float>(const IterParams<float>&, float*, int64_t, int, cudaStream_t);
 template cudaError_t launch_pd_finalize<double>(const IterParams<double>&, float*, int64_t, int, cudaStream_t);
 
