@@ -263,7 +263,7 @@ def solve_batch(problems, gammas_list, opts: Opts | None = None, want_U: bool = 
     gs = [np.ascontiguousarray(g, dtype=np.float64) for g in gammas_list]
     if len(gs) != k:
         raise ValueError("one gamma sequence per problem")
-    Us, Ls, keep = [], [], []
+    Us, Ls = [], []
     stats = [(GammaStats * max(g.size, 1))() for g in gs]
     for pb, g in zip(problems, gs):
         U = L = None
