@@ -545,14 +545,18 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{steps_o} literal FP64 MM steps (exact projection) of the oracle at the middle gamma, "
                          f"{el:.1f} s, same edges"}
+    # device bytes the iteration touches: X, Y_0, two (hi, lo) slots of A, two Delta slots,
+    # the output staging row block, and the two missing-data offsets when there is a mask
+    ld = (p + 31) // 32 * 32
+    ws_mb = n * ld * (4 * (1 + 1 + 4 + 2 + 1) + (8 if W["mask"] is not None else 0)) / 1e6
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": W["desc"], "n": n, "p": p, "edges": m, "gammas": G,
                            "iters_per_step": int(statistics.median(iters)),
-                           "l2": "working set of the iteration (~360 MB) exceeds L2 and a 256 MB buffer is written "
-                                 "between timed steps", "parallelism": f"replicas x{ws}"},
+                           "l2": f"working set of the iteration ~{ws_mb:.0f} MB; a 256 MB buffer is written "
+                                 "between timed steps to flush L2", "parallelism": f"replicas x{ws}"},
                 "solves_per_s": ws / t_max,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                              "frac": achieved / peaks.get("hbm_gbs"), "traffic": traffic,
