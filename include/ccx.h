@@ -28,7 +28,15 @@
  *  - All GPU work of a problem runs on the stream given at creation (NULL =
  *    the legacy default stream); calls that return results synchronise that
  *    stream before returning.
- *  - A ccx_problem may be used by one host thread at a time.
+ *  - A ccx_problem may be used by one host thread at a time (a problem
+ *    submitted to a server belongs to the server until ccx_wait returns).
+ *
+ * Beyond one path: ccx_solve_batch (several problems together),
+ * ccx_server_* (continuous batching with admission by device memory),
+ * ccx_build_knn_composite (genetic + geographic weights),
+ * ccx_min_connected_k, ccx_principal_axes / ccx_solve_path_projected, and
+ * instrumentation calls (ccx_time_iterations, ccx_kernel_launches,
+ * ccx_sweep_plan) that have no counterpart in the paper.
  */
 #ifndef CCX_H
 #define CCX_H

@@ -1,6 +1,10 @@
 // C ABI of the convex-clustering solver (include/ccx.h) and its host runtime:
-// input validation, device buffers, the warm-started gamma path driven by a
-// captured CUDA graph of MM iterations, per-gamma outputs and labels.
+// input validation; device buffers; the work layout of the iteration kernel
+// (plan_sweeps); the warm-started gamma path as a resumable runner driving
+// captured CUDA graphs of MM iterations, with the predictor between gammas and
+// per-gamma outputs and labels; the batch driver and the serving scheduler
+// built on the same runner; the kNN, connectivity and principal-axis entry
+// points.
 #include <cuda_runtime.h>
 
 #include <algorithm>
