@@ -420,3 +420,27 @@ def test_principal_axes_closed_forms():
     # scores: the centred data itself projects to its coordinates along the axes
     S = O.project_path(X, X, None, A)
     assert np.allclose(np.abs(S), np.abs(Z @ np.eye(3)), atol=1e-7)
+
+
+def test_fusion_scale_is_the_two_point_threshold():
+    """For one edge the scale is the mu at which Eq. 1 fuses the pair: below it the exact
+    minimiser (dual solver, independent of the oracle) keeps the points apart, above it merges them."""
+    X = np.array([[0.0, 1.0, -2.0], [3.0, -1.0, 0.5]])
+    w = 0.7
+    g0 = O.fusion_scale(X, None, [0], [1], [w])
+    assert g0 == pytest.approx(np.linalg.norm(X[0] - X[1]) / (2 * w), rel=1e-15)
+    U_lo, gap_lo = pins.convex_clustering_minimizer(X, [0], [1], [w], 0.98 * g0)
+    U_hi, gap_hi = pins.convex_clustering_minimizer(X, [0], [1], [w], 1.02 * g0)
+    assert np.linalg.norm(U_lo[0] - U_lo[1]) > 0.01 * np.linalg.norm(X[0] - X[1])
+    assert np.linalg.norm(U_hi[0] - U_hi[1]) < 1e-8
+    # several edges: the median of the per-edge thresholds (odd count: the middle one)
+    Xs = np.array([[0.0], [1.0], [3.0], [7.0]])
+    g = O.fusion_scale(Xs, None, [0, 1, 2], [1, 2, 3], [1.0, 0.5, 2.0])
+    assert g == pytest.approx(sorted([1 / 2, 2 / 1, 4 / 4])[1])
+
+
+def test_fill_missing_hand_example():
+    X = np.array([[1.0, 9.0], [3.0, 2.0], [8.0, 4.0]])
+    mask = np.array([[1, 0], [1, 1], [0, 1]], np.uint8)
+    Y = O.fill_missing(X, mask)
+    assert Y.tolist() == [[1.0, 3.0], [3.0, 2.0], [2.0, 4.0]]
