@@ -292,6 +292,72 @@ def test_knn_weights_hand_example():
     assert np.allclose(w, [r[3] for r in g["B"]], rtol=1e-15)
 
 
+def test_knn_automatic_phi_hand_example():
+    """phi = "auto" is one over the median squared distance of the union edges (odd and even edge
+    counts), worked by hand in knn_line.txt cases C and D."""
+    g = _golden_knn()
+    X = np.array([[0.0], [1.0], [3.0], [7.0]])
+    ei, ej, w, d2, phi = O.knn_gaussian_weights(X, None, 1, "auto", False)
+    assert phi == 0.25
+    assert [(a, b) for a, b, _, _ in g["C"]] == list(zip(ei.tolist(), ej.tolist()))
+    assert np.allclose(w, [r[3] for r in g["C"]], rtol=1e-15, atol=0)
+    X = np.array([[0.0], [1.0], [3.0], [7.0], [15.0]])
+    ei, ej, w, d2, phi = O.knn_gaussian_weights(X, None, 1, "auto", True)
+    assert phi == pytest.approx(0.1, rel=1e-15)
+    assert [(a, b) for a, b, _, _ in g["D"]] == list(zip(ei.tolist(), ej.tolist()))
+    assert d2.tolist() == [r[2] for r in g["D"]]
+    assert np.allclose(w, [r[3] for r in g["D"]], rtol=1e-14, atol=0)
+    # the composite rule with alpha = 1 reads phi the same way
+    cw = O.knn_composite_weights(X, None, np.zeros((5, 2)), 1.0, 1, "auto", True)
+    assert cw[4] == pytest.approx(0.1, rel=1e-15) and np.allclose(cw[2], w, rtol=1e-14, atol=0)
+
+
+def test_pd_constants_hand_example():
+    """rho = rho_scale (||Y_c||_F + mu ||w||_2) and eps = (eps_rel ||Y_c||_F)^2 on a 3 x 2 example
+    worked by hand.  Y_0 = [[1, 2], [3, 0], [5, 4]] has column means (3, 2), so
+    Y_c = [[-2, 0], [0, -2], [2, 2]] and ||Y_c||_F = 4 (the uncentred norm is sqrt(55));
+    w = (3, 4) has ||w||_2 = 5 (||w||_1 = 7).  With mu = 0.5 and the defaults rho_scale = 2,
+    eps_rel = 1e-3: rho = 2 (4 + 2.5) = 13, eps = (4e-3)^2 = 1.6e-5."""
+    Y0 = np.array([[1.0, 2.0], [3.0, 0.0], [5.0, 4.0]])
+    w = np.array([3.0, 4.0])
+    rho, eps = O.pd_constants(Y0, w, 0.5)
+    assert rho == pytest.approx(13.0, rel=1e-15)
+    assert eps == pytest.approx(1.6e-5, rel=1e-12)
+    # the slips this rules out: no centring, or the 1-norm of w
+    assert abs(rho - 2.0 * (np.sqrt(55.0) + 2.5)) > 1.0 and abs(rho - 2.0 * (4.0 + 3.5)) > 1.0
+    assert abs(eps - (1e-3 * np.sqrt(55.0)) ** 2) > 1e-6
+    rho3, eps3 = O.pd_constants(Y0, w, 0.5, rho_scale=3.0, eps_rel=1e-2)
+    assert rho3 == pytest.approx(19.5, rel=1e-15) and eps3 == pytest.approx(1.6e-3, rel=1e-12)
+    # translating the data (a column shift) leaves both unchanged: only Y_c enters
+    r2, e2 = O.pd_constants(Y0 + np.array([10.0, -7.0]), w, 0.5)
+    assert r2 == pytest.approx(rho, rel=1e-14) and e2 == pytest.approx(eps, rel=1e-12)
+    # degenerate data (all rows equal): rho = rho_scale, eps = eps_rel^2
+    r0, e0 = O.pd_constants(np.ones((4, 3)), w, 0.0)
+    assert r0 == 2.0 and e0 == pytest.approx(1e-6, rel=1e-15)
+
+
+def test_pd_constants_bound_a_lipschitz_constant_of_the_loss():
+    """rho / rho_scale bounds the gradient norm of 1/2 ||Y - U||^2 + mu sum w ||v|| wherever U lies
+    between Y_0 and its centroid (U = Y_0 - t Y_c, 0 <= t <= 1) and V has no zero row; so
+    rho > that Lipschitz constant, as the paper's exact-penalty argument asks."""
+    rng = np.random.default_rng(3)
+    Y0 = rng.normal(size=(7, 4)) + 5.0
+    w = rng.uniform(0.1, 2.0, 9)
+    mu = 0.8
+    rho, _ = O.pd_constants(Y0, w, mu)
+    Yc = Y0 - Y0.mean(axis=0)
+    for t in np.linspace(0.0, 1.0, 11):
+        U = Y0 - t * Yc
+        V = rng.normal(size=(w.size, 4))
+        gU = U - Y0
+        gV = mu * w[:, None] * V / np.linalg.norm(V, axis=1, keepdims=True)
+        gnorm = np.sqrt(np.sum(gU * gU) + np.sum(gV * gV))
+        assert gnorm <= rho / 2.0 * (1 + 1e-12)
+        # the V part is at its maximum mu ||w||_2 for every V; the U part reaches ||Y_c||_F at t = 1
+        assert np.sqrt(np.sum(gV * gV)) == pytest.approx(mu * np.linalg.norm(w), rel=1e-13)
+    assert np.linalg.norm(Yc) + mu * np.linalg.norm(w) == pytest.approx(rho / 2.0, rel=1e-15)
+
+
 def test_knn_union_properties():
     X, _ = synth.gaussian_mixture(40, 5, 3, seed=2)
     ei, ej, w, d2, _ = O.knn_gaussian_weights(X, None, 4, 0.3, True)
