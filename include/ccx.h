@@ -34,7 +34,8 @@
  * Beyond one path: ccx_solve_batch (several problems together),
  * ccx_server_* (continuous batching with admission by device memory),
  * ccx_build_knn_composite (genetic + geographic weights),
- * ccx_min_connected_k, ccx_principal_axes / ccx_solve_path_projected, and
+ * ccx_min_connected_k, ccx_principal_axes / ccx_solve_path_projected,
+ * ccx_shard_* (one problem split by columns), and
  * instrumentation calls (ccx_time_iterations, ccx_kernel_launches,
  * ccx_sweep_plan) that have no counterpart in the paper.
  */
@@ -104,6 +105,19 @@ typedef struct {
                           arrays in shared memory when they fit beside the rows of a slice, and in
                           global memory otherwise; 1: always in global memory.  Results are
                           identical either way (same arithmetic in the same order). */
+    int slice_variant; /* staging of the iteration kernel's column slices: 0 (default) automatic;
+                          1: the next slice is staged while the current one is processed (double
+                          buffer) whenever both fit in shared memory; 2: one buffer.  Results are
+                          identical in every case. */
+    int max_ctas;      /* 0 (default): the iteration kernel runs one CTA per SM, at most one per
+                          4-column slice; > 0 caps its grid, so that each CTA processes more slices
+                          (or a problem leaves SMs to others).  Results agree within the rounding of
+                          the per-CTA float partial sums, which the grid size changes. */
+    double fuse_delta; /* the V update returns zero when gamma w_ij d >= rho ||b_ij||; when the two
+                          sides differ by at most fuse_delta rho ||b_ij||, ||b_ij|| is recomputed in
+                          double from the rows of the projection before the decision, so a fuse
+                          decision does not rest on the rounding of float partial sums.  Default
+                          1e-5; 0 disables the recompute. */
 } ccx_opts;
 
 /* Per-gamma statistics. */
@@ -119,6 +133,9 @@ typedef struct {
     double d_final;    /* d_m of the last iteration */
     double err_est;    /* estimated relative error of U at stop */
     double seconds;    /* wall time of this gamma, including its output copies */
+    int n_recomputed;  /* edges whose fuse decision at the returned iterate was taken from the double
+                          recompute of ||b_ij|| (see ccx_opts.fuse_delta) */
+    long long recomputes;  /* double recomputes of ||b_ij|| over all iterations of this gamma */
 } ccx_gamma_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -248,6 +265,16 @@ ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, co
                           float* U_out, int32_t* labels_out, ccx_gamma_stats* stats);
 
 /*
+ * ccx_solve_path, also writing each gamma's fused flags (the edges whose V
+ * update returned exactly zero at the returned iterate, Methods: the block
+ * soft-threshold; the labels are the connected components of these edges):
+ *   fused_out : NULL, or n_gamma x n_edges bytes (1 = fused), host or device,
+ *               edges in the order of ccx_get_edges.
+ */
+ccx_status ccx_solve_path_fused(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts,
+                                float* U_out, int32_t* labels_out, uint8_t* fused_out, ccx_gamma_stats* stats);
+
+/*
  * Serving: a background scheduler that runs submitted path solves while the
  * caller keeps submitting (the paper has no serving layer; each job is one
  * ccx_solve_path).  Jobs that arrive while others are on the GPU are admitted
@@ -326,6 +353,51 @@ ccx_status ccx_solve_path_projected(ccx_problem* pr, const double* gammas, int n
 ccx_status ccx_solve_batch(ccx_problem* const* probs, int n_probs, const double* const* gammas, const int* n_gamma,
                            const ccx_opts* opts, float* const* U_out, int32_t* const* labels_out,
                            ccx_gamma_stats* const* stats, int max_active, ccx_status* status);
+
+/*
+ * Feature-sharded iteration: one problem split by columns, e.g. over several
+ * GPUs.  The paper's U update and its projection equations act on each column
+ * separately (Methods, "The Proximal Distance Algorithm": the U-update display
+ * and the stationarity equations of the block descent); only the per-edge
+ * ||b_ij||^2 of the V update, the two pieces of d_m (Eq. 5) and the norms of
+ * the stopping rule are sums over all columns.  A shard is a problem created
+ * from a block of columns of X (and of the mask) and given the whole
+ * problem's edge set (ccx_set_edges with the same arrays on every shard).
+ *
+ *   ccx_shard_norms       : this shard's ||Y_c||_F^2 and ||Y_0||_F^2 (sums over
+ *                           its columns).  Sum them over the shards once.
+ *   ccx_shard_begin_gamma : start penalty gamma (the shards' gammas must agree);
+ *                           yc_sq_total / y0_sq_total are those sums, which fix
+ *                           rho, eps and the error scale as for the whole problem.
+ *                           The first call continues from the problem's
+ *                           warm-start state (U = Y_0, V = 0 for a new problem or
+ *                           after ccx_reset_path); later calls continue the path,
+ *                           with the predictor of ccx_opts.extrapolate.
+ *   ccx_shard_partials    : one MM iteration's column work on this shard, then
+ *                           its partial sums in a fixed order into part (device
+ *                           memory, *len doubles on entry, at least the size;
+ *                           part = NULL: *len receives the size).
+ *   exchange (the caller) : row s of an n_shards x len device array holds
+ *                           shard s's part (an all-gather in shard order).
+ *   ccx_shard_reduce      : the iteration's reduction on the summed partials
+ *                           (fixed shard order, so every shard reaches the same
+ *                           d_m, fuse decisions and stopping state).  done: NULL,
+ *                           or receives whether this gamma has stopped (the host
+ *                           then waits for the GPU); all shards stop together.
+ *   ccx_shard_end_gamma   : this shard's columns of U (n x p_shard floats, host
+ *                           or device), the labels (the same on every shard) and
+ *                           the stats, as in ccx_solve_path.
+ * With one shard the result is bit-identical to ccx_solve_path with the same
+ * options; with several it agrees within the rounding of the partial sums.
+ * All calls are ordered on the problem's stream; none blocks the host except
+ * ccx_shard_reduce with done != NULL and ccx_shard_end_gamma.
+ */
+ccx_status ccx_shard_norms(const ccx_problem* pr, double* yc_sq, double* y0_sq);
+ccx_status ccx_shard_begin_gamma(ccx_problem* pr, double gamma, const ccx_opts* opts, double yc_sq_total,
+                                 double y0_sq_total);
+ccx_status ccx_shard_partials(ccx_problem* pr, double* part, int64_t* len);
+ccx_status ccx_shard_reduce(ccx_problem* pr, const double* parts, int n_shards, int* done);
+ccx_status ccx_shard_end_gamma(ccx_problem* pr, float* U_out, int32_t* labels_out, ccx_gamma_stats* stats);
 
 /* Forget the warm-start state: the next ccx_solve_path starts from Y_0, V = 0. */
 ccx_status ccx_reset_path(ccx_problem* pr);

@@ -35,13 +35,15 @@ class KnnRule(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("rho_scale", C.c_double), ("eps_rel", C.c_double), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("accelerate", C.c_int), ("chunk", C.c_int), ("extrapolate", C.c_int),
-                ("stream_edges", C.c_int)]
+                ("stream_edges", C.c_int), ("slice_variant", C.c_int), ("max_ctas", C.c_int),
+                ("fuse_delta", C.c_double)]
 
 
 class GammaStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("n_fused", C.c_int), ("n_clusters", C.c_int),
                 ("gamma", C.c_double), ("rho", C.c_double), ("eps", C.c_double), ("d_final", C.c_double),
-                ("err_est", C.c_double), ("seconds", C.c_double)]
+                ("err_est", C.c_double), ("seconds", C.c_double), ("n_recomputed", C.c_int),
+                ("recomputes", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,11 +63,17 @@ _sigs = {
     "ccx_fusion_scale": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_fusion_scale_noalloc": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "ccx_solve_path": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P]),
+    "ccx_solve_path_fused": (C.c_int, [_P, _P, C.c_int, C.POINTER(Opts), _P, _P, _P, _P]),
     "ccx_solve_batch": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(Opts), _P, _P, _P, C.c_int, _P]),
     "ccx_server_create": (C.c_int, [C.POINTER(Opts), C.c_size_t, C.c_int, C.POINTER(_P)]),
     "ccx_submit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, C.POINTER(C.c_uint64)]),
     "ccx_wait": (C.c_int, [_P, C.c_uint64, C.c_int64]),
     "ccx_server_destroy": (C.c_int, [_P]),
+    "ccx_shard_norms": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ccx_shard_begin_gamma": (C.c_int, [_P, C.c_double, C.POINTER(Opts), C.c_double, C.c_double]),
+    "ccx_shard_partials": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
+    "ccx_shard_reduce": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
+    "ccx_shard_end_gamma": (C.c_int, [_P, _P, _P, C.POINTER(GammaStats)]),
     "ccx_reset_path": (C.c_int, [_P]),
     "ccx_problem_destroy": (C.c_int, [_P]),
     "ccx_time_iterations": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
@@ -225,11 +233,13 @@ def fusion_scale_noalloc(h) -> float:
 
 
 def solve_path(h, gammas, n: int, p: int, opts: Opts | None = None, want_U: bool = True,
-               want_labels: bool = True, device: bool = False, U_out=None, labels_out=None):
+               want_labels: bool = True, device: bool = False, U_out=None, labels_out=None, fused_out=None):
     """Solve the warm-started path.  Returns (U (G x n x p float32), labels (G x n int32), stats list, status).
 
     With device=True the outputs are CUDA torch tensors written directly by the
-    library; otherwise numpy arrays.  Preallocated outputs may be passed.
+    library; otherwise numpy arrays.  Preallocated outputs may be passed;
+    fused_out (G x n_edges uint8, numpy or torch) also receives each gamma's
+    fused flags (ccx_solve_path_fused).
     """
     g = np.ascontiguousarray(gammas, dtype=np.float64)
     G = g.size
@@ -248,7 +258,13 @@ def solve_path(h, gammas, n: int, p: int, opts: Opts | None = None, want_U: bool
     lp, _ = _ptr(labels_out, np.int32) if labels_out is not None else (None, None)
     stats = (GammaStats * max(G, 1))()
     o = C.byref(opts) if opts is not None else None
-    st = _check(_lib.ccx_solve_path(h, g.ctypes.data, G, o, up, lp, stats), allow=(0, 4))
+    if fused_out is not None:
+        fp, _fk = _ptr(fused_out, np.uint8)
+        if not _is_torch(fused_out) and fp != fused_out.ctypes.data:
+            raise ValueError("fused_out must be a contiguous uint8 array")
+        st = _check(_lib.ccx_solve_path_fused(h, g.ctypes.data, G, o, up, lp, fp, stats), allow=(0, 4))
+    else:
+        st = _check(_lib.ccx_solve_path(h, g.ctypes.data, G, o, up, lp, stats), allow=(0, 4))
     return U_out, labels_out, [stats[k].as_dict() for k in range(G)], st
 
 
@@ -343,6 +359,112 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------- feature shards
+def shard_norms(h):
+    """(||Y_c||_F^2, ||Y_0||_F^2) of this column shard."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.ccx_shard_norms(h, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def shard_begin_gamma(h, gamma: float, opts: Opts | None, yc_sq_total: float, y0_sq_total: float) -> None:
+    o = C.byref(opts) if opts is not None else None
+    _check(_lib.ccx_shard_begin_gamma(h, float(gamma), o, float(yc_sq_total), float(y0_sq_total)))
+
+
+def shard_partials_len(h) -> int:
+    n = C.c_int64(0)
+    _check(_lib.ccx_shard_partials(h, None, C.byref(n)))
+    return int(n.value)
+
+
+def shard_partials(h, part) -> None:
+    """One iteration's column work; its partial sums into `part` (CUDA float64 tensor)."""
+    n = C.c_int64(part.numel())
+    _check(_lib.ccx_shard_partials(h, part.data_ptr(), C.byref(n)))
+
+
+def shard_reduce(h, parts, want_done: bool = True):
+    """The iteration's reduction over `parts` (CUDA float64 tensor, n_shards x len, shard order)."""
+    d = C.c_int(0)
+    _check(_lib.ccx_shard_reduce(h, parts.data_ptr(), int(parts.shape[0]), C.byref(d) if want_done else None))
+    return bool(d.value) if want_done else None
+
+
+def shard_end_gamma(h, n: int, p: int):
+    U = np.empty((n, p), np.float32)
+    L = np.empty(n, np.int32)
+    st = GammaStats()
+    _check(_lib.ccx_shard_end_gamma(h, U.ctypes.data, L.ctypes.data, C.byref(st)))
+    return U, L, st.as_dict()
+
+
+def allgather_parts(part, group=None):
+    """Exchange of the feature-sharded iteration across ranks (one shard per rank):
+    every rank's partial vector, stacked in rank order (an all-gather; the sum in
+    that fixed order happens inside ccx_shard_reduce)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size(group)
+    bufs = [torch.empty_like(part) for _ in range(ws)]
+    dist.all_gather(bufs, part, group=group)
+    return torch.stack(bufs)
+
+
+def ordered_sum(values, group=None):
+    """Sum of one float per rank in rank order, identical on every rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in np.atleast_1d(values)], dtype=torch.float64)
+    ws = dist.get_world_size(group)
+    bufs = [torch.empty_like(t) for _ in range(ws)]
+    dist.all_gather(bufs, t, group=group)
+    out = torch.zeros_like(t)
+    for b in bufs:
+        out += b
+    return out.numpy()
+
+
+def solve_path_sharded(shards, gammas, opts: Opts | None = None, exchange=None, check_every: int = 16,
+                       norms=None):
+    """Warm-started path of one problem split by columns into `shards` (Problems on
+    column blocks with the same edge set), driven iteration by iteration through
+    the ccx_shard_* calls.  exchange(list of local partial tensors) returns the
+    n_shards x len tensor in shard order (default: all shards in this process,
+    stacked); norms: the whole problem's (||Y_c||^2, ||Y_0||^2) (default: the sum
+    over `shards`).  Returns ([U of each shard per gamma], labels per gamma, stats
+    of the first shard per gamma)."""
+    import torch
+    if norms is None:
+        nn = [shard_norms(s.h) for s in shards]
+        norms = (sum(a for a, _ in nn), sum(b for _, b in nn))
+    L = shard_partials_len(shards[0].h)
+    parts = [torch.empty(L, dtype=torch.float64, device="cuda") for _ in shards]
+    if exchange is None:
+        exchange = torch.stack
+    Us, labels, stats = [[] for _ in shards], [], []
+    for g in np.asarray(gammas, dtype=np.float64):
+        for s in shards:
+            shard_begin_gamma(s.h, g, opts, norms[0], norms[1])
+        it = 0
+        while True:
+            for s, part in zip(shards, parts):
+                shard_partials(s.h, part)
+            allp = exchange(parts)
+            it += 1
+            check = it % check_every == 0
+            done = [shard_reduce(s.h, allp, want_done=check) for s in shards]
+            if check and all(done):
+                break
+        for k, s in enumerate(shards):
+            U, lab, st = shard_end_gamma(s.h, s.n, s.p)
+            Us[k].append(U)
+            if k == 0:
+                labels.append(lab)
+                stats.append(st)
+    return Us, labels, stats
 
 
 def reset_path(h) -> None:

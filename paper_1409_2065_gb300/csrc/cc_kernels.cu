@@ -6,7 +6,10 @@
 // happens, then full compression and a rank scan.  Roots only ever point to
 // smaller indices, so every component ends at its minimum index whatever the
 // order in which threads hook: the labels are deterministic.  The loop is
-// bounded by n + 1 rounds (each productive round removes at least one root).
+// bounded by n + 1 rounds.  A round in which no thread hooks proves every fused
+// edge joins one component; if even the last round hooked, the labels are not
+// proven and the component count is written as -1, which the host reports as
+// an error instead of returning the labels.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -38,6 +41,8 @@ __global__ void __launch_bounds__(kCcThreads) cc_kernel(int n, int m, const int*
     for (int i = threadIdx.x; i < n; i += blockDim.x) parent[i] = i;
     __syncthreads();
     volatile int* vp = parent;
+    __shared__ int settled;
+    if (threadIdx.x == 0) settled = 0;
     for (int round = 0; round <= n; ++round) {
         if (threadIdx.x == 0) changed = 0;
         __syncthreads();
@@ -54,9 +59,13 @@ __global__ void __launch_bounds__(kCcThreads) cc_kernel(int n, int m, const int*
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) parent[i] = find_root(vp, i);
         __syncthreads();
-        if (!changed) break;
+        if (!changed) {
+            if (threadIdx.x == 0) settled = 1;
+            break;
+        }
         __syncthreads();
     }
+    __syncthreads();
     // ranks of the roots: block scan of root flags in index order
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -92,7 +101,7 @@ __global__ void __launch_bounds__(kCcThreads) cc_kernel(int n, int m, const int*
         const int r = parent[i];
         if (r != i) labels[i] = labels[r];
     }
-    if (threadIdx.x == 0) *n_clusters = carry;
+    if (threadIdx.x == 0) *n_clusters = settled ? carry : -1;
 }
 
 }  // namespace

@@ -81,7 +81,12 @@ cudaError_t dalloc(T** p, size_t count) {
 
 }  // namespace
 
+namespace {
+struct ShardState;
+}  // namespace
+
 struct ccx_problem {
+    ShardState* shard = nullptr;  // feature-sharded iteration state (ccx_shard_*), created on first use
     int device = 0;
     cudaStream_t user = nullptr;
     cudaStream_t work = nullptr;
@@ -152,7 +157,13 @@ struct ccx_problem {
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     int graph_stream = 0;        // stream_edges the captured graph was built with
+    int graph_variant = -1;      // slice_variant, grid and fuse_delta the captured graph was built with
+    int graph_G = 0;
+    double graph_delta = -1.0;
     int stream_edges = 0;        // from the options of the current call
+    int variant = 0;
+    int max_ctas = 0;
+    double delta_fuse = 1e-5;
 };
 
 namespace {
@@ -554,6 +565,11 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.le = pr->le;
     P.nslots = pr->nslots;
     P.stream_edges = pr->stream_edges;
+    P.delta_fuse = pr->delta_fuse;
+    P.ext_part = nullptr;
+    P.n_ext = 0;
+    P.ext_len = 0;
+    P.p = (int)pr->p;
     P.ei = pr->d_ei;
     P.ej = pr->d_ej;
     P.w = pr->d_w;
@@ -590,14 +606,43 @@ ccx_status check_limits(ccx_problem* pr) {
     return CCX_OK;
 }
 
+// grid of the iteration kernel: one CTA per SM, at most one per slice, capped by max_ctas
+int grid_of(const ccx_problem* pr) {
+    const int nsl = (int)((pr->p + kSliceCols - 1) / kSliceCols);
+    int G = std::min(nsl, pr->num_sms);
+    if (pr->max_ctas > 0) G = std::min(G, pr->max_ctas);
+    return std::max(G, 1);
+}
+
+// The options of a call that shape the iteration kernel's launch.
+void apply_opts(ccx_problem* pr, const ccx_opts& o) {
+    pr->stream_edges = o.stream_edges ? 1 : 0;
+    pr->variant = o.slice_variant;
+    pr->max_ctas = o.max_ctas;
+    pr->delta_fuse = o.fuse_delta;
+}
+
 ccx_status ensure_path(ccx_problem* pr) {
-    if (pr->path_ready) return CCX_OK;
+    if (pr->path_ready) {
+        // a changed grid cap resizes the per-CTA partial buffers (the path state is kept)
+        const int G = grid_of(pr);
+        if (G != pr->G) {
+            cudaFree(pr->Pnb);
+            cudaFree(pr->Ps);
+            pr->Pnb = nullptr;
+            pr->Ps = nullptr;
+            pr->G = G;
+            CUDA_TRY(dalloc(&pr->Pnb, (size_t)G * pr->le * kSliceThreads));
+            CUDA_TRY(dalloc(&pr->Ps, (size_t)G * kNumScalarPartials));
+        }
+        return CCX_OK;
+    }
     const bool fp64 = pr->precision == CCX_FP64;
     const size_t es = fp64 ? sizeof(double) : sizeof(float);
     const size_t nl = (size_t)pr->n * pr->ld;
     const int m = (int)pr->ei.size();
     pr->nslices = (int)((pr->p + kSliceCols - 1) / kSliceCols);
-    pr->G = std::min(pr->nslices, pr->num_sms);
+    pr->G = grid_of(pr);
     for (int k = 0; k < 2; ++k) {
         CUDA_TRY(cudaMalloc(&pr->A[k], es * nl));
         CUDA_TRY(cudaMalloc(&pr->Dl[k], es * nl));
@@ -617,7 +662,7 @@ ccx_status ensure_path(ccx_problem* pr) {
     CUDA_TRY(dalloc(&pr->Ps, (size_t)pr->G * kNumScalarPartials));
     CUDA_TRY(dalloc(&pr->nb, m));
     CUDA_TRY(dalloc(&pr->fused, m));
-    CUDA_TRY(dalloc(&pr->Rf, 2 * (size_t)pd_reduce_blocks(pr->le)));
+    CUDA_TRY(dalloc(&pr->Rf, 3 * (size_t)pd_reduce_blocks(pr->le)));
     CUDA_TRY(dalloc(&pr->st, 1));
     CUDA_TRY(cudaMallocHost(&pr->st_host, 2 * sizeof(PdState)));
     CUDA_TRY(dalloc(&pr->Ustage, (size_t)pr->n * pr->p));
@@ -631,8 +676,13 @@ ccx_status ensure_path(ccx_problem* pr) {
     return CCX_OK;
 }
 
+bool graph_stale(const ccx_problem* pr, int chunk) {
+    return !pr->graph || pr->graph_chunk != chunk || pr->graph_stream != pr->stream_edges ||
+           pr->graph_variant != pr->variant || pr->graph_G != pr->G || pr->graph_delta != pr->delta_fuse;
+}
+
 ccx_status build_graph(ccx_problem* pr, int chunk) {
-    if (pr->graph && pr->graph_chunk == chunk && pr->graph_stream == pr->stream_edges) return CCX_OK;
+    if (!graph_stale(pr, chunk)) return CCX_OK;
     if (pr->graph) {
         cudaGraphExecDestroy(pr->graph);
         pr->graph = nullptr;
@@ -642,8 +692,10 @@ ccx_status build_graph(ccx_problem* pr, int chunk) {
     CUDA_TRY(cudaStreamBeginCapture(pr->work, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
     for (int k = 0; k < chunk && err == cudaSuccess; ++k) {
-        if (pr->precision == CCX_FP64) err = launch_pd_iteration<double>(make_params<double>(pr), pr->work);
-        else err = launch_pd_iteration<float>(make_params<float>(pr), pr->work);
+        if (pr->precision == CCX_FP64)
+            err = launch_pd_iteration_variant<double>(make_params<double>(pr), pr->variant, pr->work);
+        else
+            err = launch_pd_iteration_variant<float>(make_params<float>(pr), pr->variant, pr->work);
     }
     cudaError_t e2 = cudaStreamEndCapture(pr->work, &g);
     g_launches.fetch_sub(2ULL * (unsigned long long)chunk, std::memory_order_relaxed);  // captured, not launched
@@ -657,6 +709,9 @@ ccx_status build_graph(ccx_problem* pr, int chunk) {
     if (err != cudaSuccess) return fail(CCX_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(err));
     pr->graph_chunk = chunk;
     pr->graph_stream = pr->stream_edges;
+    pr->graph_variant = pr->variant;
+    pr->graph_G = pr->G;
+    pr->graph_delta = pr->delta_fuse;
     return CCX_OK;
 }
 
@@ -672,10 +727,11 @@ struct PathRun {
     ccx_opts o{};
     float* U_out = nullptr;
     int32_t* labels_out = nullptr;
+    uint8_t* fused_out = nullptr;  // n_gamma x m fused flags, or NULL
     ccx_gamma_stats* stats = nullptr;
     int pc_q = 0;                  // > 0: write the scores on the principal axes instead of U
     float* scores_out = nullptr;
-    bool u_dev = false, l_dev = false, s_dev = false;
+    bool u_dev = false, l_dev = false, s_dev = false, f_dev = false;
     enum Phase { kIterate, kOutputs, kDone } phase = kDone;
     int g = 0, launched = 0, checked = 0;
     double rho = 0.0, eps = 0.0;
@@ -763,12 +819,13 @@ ccx_status path_open(PathRun& r) {
     // The first launch of each kernel variant raises its shared-memory limit,
     // which must not happen under capture: launch once on a finished state
     // (done = 1, so every kernel returns at once) before capturing.
-    if (!pr->graph || pr->graph_stream != pr->stream_edges) CUDA_TRY(launch_pd_iteration<R>(P, pr->work));
+    if (graph_stale(pr, r.o.chunk)) CUDA_TRY(launch_pd_iteration_variant<R>(P, pr->variant, pr->work));
     s = build_graph(pr, r.o.chunk);
     if (s != CCX_OK) return s;
     r.u_dev = is_device_ptr(r.U_out);
     r.l_dev = is_device_ptr(r.labels_out);
     r.s_dev = is_device_ptr(r.scores_out);
+    r.f_dev = is_device_ptr(r.fused_out);
     r.g = 0;
     r.all_conv = true;
     r.conv_hist[0] = r.conv_hist[1] = r.conv_hist[2] = 0;
@@ -841,6 +898,9 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
         if (r.labels_out && !r.l_dev)
             CUDA_TRY(cudaMemcpyAsync(r.labels_out + (size_t)g * pr->n, pr->Lstage, sizeof(int) * pr->n,
                                      cudaMemcpyDeviceToHost, pr->work));
+        if (r.fused_out && P.m > 0)
+            CUDA_TRY(cudaMemcpyAsync(r.fused_out + (size_t)g * P.m, pr->fused, (size_t)P.m,
+                                     r.f_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, pr->work));
         CUDA_TRY(cudaMemcpyAsync(pr->h_ncl, pr->d_ncl, sizeof(int), cudaMemcpyDeviceToHost, pr->work));
         CUDA_TRY(cudaEventRecord(pr->ev_out, pr->work));
         r.phase = PathRun::kOutputs;
@@ -854,6 +914,9 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
             CUDA_TRY(q);
         }
         *progressed = true;
+        if (*pr->h_ncl < 0)
+            return fail(CCX_ECUDA, "gamma %d: the connected-components pass over the fused edges did not settle "
+                                   "within n + 1 rounds; labels not written", r.g);
         if (r.stats) {
             ccx_gamma_stats& S = r.stats[r.g];
             S.iters = r.final.iter;
@@ -865,6 +928,8 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
             S.eps = r.eps;
             S.d_final = r.final.d_last;
             S.err_est = r.final.err_est;
+            S.n_recomputed = r.final.n_recomputed;
+            S.recomputes = r.final.recompute_total;
             S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t0).count();
         }
         ++r.g;
@@ -906,6 +971,9 @@ ccx_status resolve_opts(const ccx_problem* pr, const ccx_opts* opts, ccx_opts* o
     if (!(o->tol > 0.0)) return fail(CCX_EINVAL, "tol must be > 0");
     if (o->max_iter < 1) return fail(CCX_EINVAL, "max_iter must be >= 1");
     if (o->chunk < 1 || o->chunk > 4096) return fail(CCX_EINVAL, "chunk must be in [1, 4096]");
+    if (o->slice_variant < 0 || o->slice_variant > 2) return fail(CCX_EINVAL, "slice_variant must be 0, 1 or 2");
+    if (o->max_ctas < 0) return fail(CCX_EINVAL, "max_ctas must be >= 0");
+    if (!(o->fuse_delta >= 0.0 && o->fuse_delta < 1.0)) return fail(CCX_EINVAL, "fuse_delta must be in [0, 1)");
     return CCX_OK;
 }
 
@@ -932,6 +1000,9 @@ void ccx_opts_default(ccx_opts* o) {
     o->chunk = 64;
     o->extrapolate = 1;
     o->stream_edges = 0;
+    o->slice_variant = 0;
+    o->max_ctas = 0;
+    o->fuse_delta = 1e-5;
 }
 
 const char* ccx_last_error(void) { return g_err.c_str(); }
@@ -1224,6 +1295,11 @@ ccx_status ccx_fusion_scale_noalloc(const ccx_problem* pr_c, double* gamma0) {
 
 ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts, float* U_out,
                           int32_t* labels_out, ccx_gamma_stats* stats) {
+    return ccx_solve_path_fused(pr, gammas, n_gamma, opts, U_out, labels_out, nullptr, stats);
+}
+
+ccx_status ccx_solve_path_fused(ccx_problem* pr, const double* gammas, int n_gamma, const ccx_opts* opts,
+                                float* U_out, int32_t* labels_out, uint8_t* fused_out, ccx_gamma_stats* stats) {
     g_err.clear();
     if (!pr) return fail(CCX_EINVAL, "problem is NULL");
     ccx_status s = check_gammas(gammas, n_gamma);
@@ -1231,12 +1307,13 @@ ccx_status ccx_solve_path(ccx_problem* pr, const double* gammas, int n_gamma, co
     PathRun r;
     s = resolve_opts(pr, opts, &r.o);
     if (s != CCX_OK) return s;
-    pr->stream_edges = r.o.stream_edges ? 1 : 0;
+    apply_opts(pr, r.o);
     r.pr = pr;
     r.gammas = gammas;
     r.n_gamma = n_gamma;
     r.U_out = U_out;
     r.labels_out = labels_out;
+    r.fused_out = fused_out;
     r.stats = stats;
     s = path_open_any(r);
     if (s != CCX_OK) return s;
@@ -1295,7 +1372,7 @@ ccx_status ccx_solve_path_projected(ccx_problem* pr, const double* gammas, int n
     if (s != CCX_OK) return s;
     s = ensure_axes(pr, q);
     if (s != CCX_OK) return s;
-    pr->stream_edges = r.o.stream_edges ? 1 : 0;
+    apply_opts(pr, r.o);
     r.pr = pr;
     r.gammas = gammas;
     r.n_gamma = n_gamma;
@@ -1355,7 +1432,7 @@ ccx_status ccx_solve_batch(ccx_problem* const* probs, int n_probs, const double*
         while ((int)active.size() < max_active && next < n_probs) {
             const int i = next++;
             g_err.clear();
-            runs[i].pr->stream_edges = runs[i].o.stream_edges ? 1 : 0;
+            apply_opts(runs[i].pr, runs[i].o);
             const ccx_status s = path_open_any(runs[i]);
             if (s != CCX_OK) {
                 st[i] = s;
@@ -1408,7 +1485,7 @@ size_t path_bytes(const ccx_problem* pr) {
     const size_t T = kSliceThreads;
     size_t b = 5 * es * nl + (fp64 ? 0 : 3 * 4 * nl) + (pr->has_mask ? 2 * es * nl : 0);
     b += 2 * es * 2 * ((size_t)pr->la + pr->le) * T;
-    b += G * (size_t)pr->le * T * 4 + G * 64 + m * 9 + 16 * (size_t)pd_reduce_blocks(pr->le);
+    b += G * (size_t)pr->le * T * 4 + G * 64 + m * 9 + 24 * (size_t)pd_reduce_blocks(pr->le);
     b += (size_t)pr->n * pr->p * 4 + (size_t)pr->n * 8 + 4096;
     return b + b / 16 + (1u << 20);   // allocation rounding
 }
@@ -1477,7 +1554,7 @@ struct ccx_server {
             }
             for (auto& j : admitted) {
                 g_err.clear();
-                j->pr->stream_edges = j->run.o.stream_edges ? 1 : 0;
+                apply_opts(j->pr, j->run.o);
                 const ccx_status st = path_open_any(j->run);
                 if (st != CCX_OK || j->run.phase == PathRun::kDone) {
                     const ccx_status fin = st != CCX_OK ? st : path_close(j->run, CCX_OK);
@@ -1612,6 +1689,218 @@ ccx_status ccx_server_destroy(ccx_server* srv) {
     return CCX_OK;
 }
 
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ feature shards
+namespace {
+
+// A problem used as one column shard of a larger problem: the gammas begun so
+// far (for the predictor between gammas), the runner that begins them, and the
+// norms of the whole problem that fix rho, eps and the error scale.
+struct ShardState {
+    PathRun run;
+    std::vector<double> hist;
+    double nyc = 0.0, ny0 = 0.0;
+    bool open = false;
+};
+
+void drop_shard(ccx_problem* pr) {
+    delete pr->shard;
+    pr->shard = nullptr;
+}
+
+// make the caller's stream wait for the work stream without blocking the host
+ccx_status leave_async(ccx_problem* pr) {
+    CUDA_TRY(cudaEventRecord(pr->ev_done, pr->work));
+    CUDA_TRY(cudaStreamWaitEvent(pr->user, pr->ev_done, 0));
+    return CCX_OK;
+}
+
+template <typename R>
+ccx_status shard_begin(ccx_problem* pr, ShardState& sh, double gamma) {
+    PathRun& r = sh.run;
+    if (!sh.open || !pr->path_started) {
+        if (!pr->path_started) {
+            const R* Y0 = std::is_same<R, double>::value ? reinterpret_cast<const R*>(pr->Y0d)
+                                                          : reinterpret_cast<const R*>(pr->Y0f);
+            CUDA_TRY(launch_pd_init<R>(make_params<R>(pr), Y0, pr->work));
+            pr->path_started = true;
+        }
+        sh.hist.clear();
+        r.conv_hist[0] = r.conv_hist[1] = r.conv_hist[2] = 0;
+        r.all_conv = true;
+        sh.open = true;
+    }
+    sh.hist.push_back(gamma);
+    r.pr = pr;
+    r.gammas = sh.hist.data();
+    r.n_gamma = (int)sh.hist.size();
+    r.g = r.n_gamma - 1;
+    // rho, eps and the error floor come from the norms of the whole problem
+    const double keep_c = pr->nyc, keep_0 = pr->ny0;
+    pr->nyc = sh.nyc;
+    pr->ny0 = sh.ny0;
+    const ccx_status s = path_begin_gamma<R>(r);
+    pr->nyc = keep_c;
+    pr->ny0 = keep_0;
+    return s;
+}
+
+template <typename R>
+ccx_status shard_end(ccx_problem* pr, ShardState& sh, float* U_out, int32_t* labels_out, ccx_gamma_stats* stats) {
+    PathRun& r = sh.run;
+    IterParams<R> P = make_params<R>(pr);
+    const bool u_dev = is_device_ptr(U_out), l_dev = is_device_ptr(labels_out);
+    if (U_out) {
+        if (u_dev) {
+            CUDA_TRY(launch_pd_finalize<R>(P, U_out, pr->p, (int)pr->p, pr->work));
+        } else {
+            CUDA_TRY(launch_pd_finalize<R>(P, pr->Ustage, pr->p, (int)pr->p, pr->work));
+            CUDA_TRY(cudaMemcpyAsync(U_out, pr->Ustage, sizeof(float) * pr->n * pr->p, cudaMemcpyDeviceToHost,
+                                     pr->work));
+        }
+    }
+    int* ldst = (labels_out && l_dev) ? labels_out : pr->Lstage;
+    CUDA_TRY(launch_fused_labels((int)pr->n, P.m, pr->d_ei, pr->d_ej, pr->fused, ldst, pr->d_ncl, pr->cc_scratch,
+                                 pr->work));
+    if (labels_out && !l_dev)
+        CUDA_TRY(cudaMemcpyAsync(labels_out, pr->Lstage, sizeof(int) * pr->n, cudaMemcpyDeviceToHost, pr->work));
+    CUDA_TRY(cudaMemcpyAsync(pr->h_ncl, pr->d_ncl, sizeof(int), cudaMemcpyDeviceToHost, pr->work));
+    CUDA_TRY(cudaMemcpyAsync(&pr->st_host[0], pr->st, sizeof(PdState), cudaMemcpyDeviceToHost, pr->work));
+    CUDA_TRY(cudaStreamSynchronize(pr->work));
+    const PdState f = pr->st_host[0];
+    if (*pr->h_ncl < 0)
+        return fail(CCX_ECUDA, "the connected-components pass over the fused edges did not settle within n + 1 "
+                               "rounds; labels not written");
+    r.conv_hist[2] = r.conv_hist[1];
+    r.conv_hist[1] = r.conv_hist[0];
+    r.conv_hist[0] = f.converged;
+    if (stats) {
+        stats->iters = f.iter;
+        stats->converged = f.converged;
+        stats->n_fused = std::max(f.n_fused, 0);
+        stats->n_clusters = *pr->h_ncl;
+        stats->gamma = r.gammas[r.g];
+        stats->rho = r.rho;
+        stats->eps = r.eps;
+        stats->d_final = f.d_last;
+        stats->err_est = f.err_est;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t0).count();
+        stats->n_recomputed = f.n_recomputed;
+        stats->recomputes = f.recompute_total;
+    }
+    return CCX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ccx_status ccx_shard_norms(const ccx_problem* pr, double* yc_sq, double* y0_sq) {
+    g_err.clear();
+    if (!pr || !yc_sq || !y0_sq) return fail(CCX_EINVAL, "NULL argument");
+    *yc_sq = pr->nyc * pr->nyc;
+    *y0_sq = pr->ny0 * pr->ny0;
+    return CCX_OK;
+}
+
+ccx_status ccx_shard_begin_gamma(ccx_problem* pr, double gamma, const ccx_opts* opts, double yc_sq_total,
+                                 double y0_sq_total) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    if (!std::isfinite(gamma) || gamma < 0.0) return fail(CCX_EINVAL, "gamma must be finite and >= 0");
+    if (!(yc_sq_total >= 0.0) || !(y0_sq_total >= 0.0) || !std::isfinite(yc_sq_total) || !std::isfinite(y0_sq_total))
+        return fail(CCX_EINVAL, "the squared norms must be finite and >= 0");
+    if (!pr->shard) pr->shard = new ShardState();
+    ShardState& sh = *pr->shard;
+    ccx_status s = resolve_opts(pr, opts, &sh.run.o);
+    if (s != CCX_OK) return s;
+    apply_opts(pr, sh.run.o);
+    s = check_limits(pr);
+    if (s != CCX_OK) return s;
+    s = enter(pr);
+    if (s != CCX_OK) return s;
+    s = ensure_path(pr);
+    if (s != CCX_OK) return s;
+    sh.nyc = std::sqrt(yc_sq_total);
+    sh.ny0 = std::sqrt(y0_sq_total);
+    s = pr->precision == CCX_FP64 ? shard_begin<double>(pr, sh, gamma) : shard_begin<float>(pr, sh, gamma);
+    if (s != CCX_OK) return s;
+    return leave_async(pr);
+}
+
+ccx_status ccx_shard_partials(ccx_problem* pr, double* part, int64_t* len) {
+    g_err.clear();
+    if (!pr || !len) return fail(CCX_EINVAL, "NULL argument");
+    const int64_t L = (int64_t)pr->le * kSliceThreads + kNumScalarPartials;
+    if (!part) {
+        *len = L;
+        return CCX_OK;
+    }
+    if (!pr->shard || !pr->shard->open || !pr->path_ready)
+        return fail(CCX_EINVAL, "ccx_shard_begin_gamma has not been called on this problem");
+    if (*len < L) return fail(CCX_EINVAL, "part holds %lld doubles, %lld needed", (long long)*len, (long long)L);
+    if (!is_device_ptr(part)) return fail(CCX_EINVAL, "part must be device memory");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    if (pr->precision == CCX_FP64) {
+        const IterParams<double> P = make_params<double>(pr);
+        CUDA_TRY(launch_pd_slice_variant<double>(P, pr->variant, pr->work));
+        CUDA_TRY(launch_pd_shard_partials<double>(P, part, pr->work));
+    } else {
+        const IterParams<float> P = make_params<float>(pr);
+        CUDA_TRY(launch_pd_slice_variant<float>(P, pr->variant, pr->work));
+        CUDA_TRY(launch_pd_shard_partials<float>(P, part, pr->work));
+    }
+    *len = L;
+    return leave_async(pr);
+}
+
+ccx_status ccx_shard_reduce(ccx_problem* pr, const double* parts, int n_shards, int* done) {
+    g_err.clear();
+    if (!pr || !parts) return fail(CCX_EINVAL, "NULL argument");
+    if (n_shards < 1) return fail(CCX_EINVAL, "n_shards must be >= 1");
+    if (!pr->shard || !pr->shard->open || !pr->path_ready)
+        return fail(CCX_EINVAL, "ccx_shard_begin_gamma has not been called on this problem");
+    if (!is_device_ptr(parts)) return fail(CCX_EINVAL, "parts must be device memory");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    const long long L = (long long)pr->le * kSliceThreads + kNumScalarPartials;
+    if (pr->precision == CCX_FP64) {
+        IterParams<double> P = make_params<double>(pr);
+        P.ext_part = parts;
+        P.n_ext = n_shards;
+        P.ext_len = L;
+        CUDA_TRY(launch_pd_reduce<double>(P, pr->work));
+    } else {
+        IterParams<float> P = make_params<float>(pr);
+        P.ext_part = parts;
+        P.n_ext = n_shards;
+        P.ext_len = L;
+        CUDA_TRY(launch_pd_reduce<float>(P, pr->work));
+    }
+    if (done) {
+        CUDA_TRY(cudaMemcpyAsync(&pr->st_host[1], pr->st, sizeof(PdState), cudaMemcpyDeviceToHost, pr->work));
+        CUDA_TRY(cudaStreamSynchronize(pr->work));
+        *done = pr->st_host[1].done;
+    }
+    return leave_async(pr);
+}
+
+ccx_status ccx_shard_end_gamma(ccx_problem* pr, float* U_out, int32_t* labels_out, ccx_gamma_stats* stats) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    if (!pr->shard || !pr->shard->open || !pr->path_ready)
+        return fail(CCX_EINVAL, "ccx_shard_begin_gamma has not been called on this problem");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    s = pr->precision == CCX_FP64 ? shard_end<double>(pr, *pr->shard, U_out, labels_out, stats)
+                                  : shard_end<float>(pr, *pr->shard, U_out, labels_out, stats);
+    if (s != CCX_OK) return s;
+    return leave(pr);
+}
+
 ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts, double* slice_ms,
                                double* reduce_ms) {
     g_err.clear();
@@ -1619,10 +1908,10 @@ ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const 
     if (!std::isfinite(gamma) || gamma < 0.0) return fail(CCX_EINVAL, "gamma must be finite and >= 0");
     if (n_iter < 1) return fail(CCX_EINVAL, "n_iter must be >= 1");
     ccx_opts o;
-    ccx_opts_default(&o);
-    if (opts) o = *opts;
-    pr->stream_edges = o.stream_edges ? 1 : 0;
-    ccx_status s = check_limits(pr);
+    ccx_status s = resolve_opts(pr, opts, &o);
+    if (s != CCX_OK) return s;
+    apply_opts(pr, o);
+    s = check_limits(pr);
     if (s != CCX_OK) return s;
     s = enter(pr);
     if (s != CCX_OK) return s;
@@ -1647,7 +1936,7 @@ ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const 
         CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, -1.0, n_iter + 1, o.accelerate, 0.0, pr->work));
         for (int k = 0; k < n_iter; ++k) {
             CUDA_TRY(cudaEventRecord(ev[3 * k], pr->work));
-            CUDA_TRY(launch_pd_slice<R>(P, pr->work));
+            CUDA_TRY(launch_pd_slice_variant<R>(P, pr->variant, pr->work));
             CUDA_TRY(cudaEventRecord(ev[3 * k + 1], pr->work));
             CUDA_TRY(launch_pd_reduce<R>(P, pr->work));
             CUDA_TRY(cudaEventRecord(ev[3 * k + 2], pr->work));
@@ -1677,6 +1966,7 @@ ccx_status ccx_reset_path(ccx_problem* pr) {
     g_err.clear();
     if (!pr) return fail(CCX_EINVAL, "problem is NULL");
     pr->path_started = false;
+    if (pr->shard) pr->shard->open = false;
     return CCX_OK;
 }
 
@@ -1686,6 +1976,7 @@ ccx_status ccx_problem_destroy(ccx_problem* pr) {
     cudaSetDevice(pr->device);
     cudaStreamSynchronize(pr->work);
     free_all(pr);
+    drop_shard(pr);
     delete pr;
     return CCX_OK;
 }

@@ -75,7 +75,8 @@ struct PdState {
     int n_fused;
     int fused_stable;     // iterations since the fused set last changed
     unsigned int counter; // arrival counter of the reduce kernel's blocks
-    int pad_;
+    int n_recomputed;     // edges of the last iteration whose fuse decision came from the FP64 recompute
+    long long recompute_total;  // FP64 recomputes over the current gamma's iterations
 };
 
 template <typename R>
@@ -114,7 +115,20 @@ struct IterParams {
     uint8_t* fused;             // per-edge fused flag of t_{m+1}
     unsigned long long* Rf;     // per reduce-block fused count / hash
     PdState* st;
-    int n, ld, ldw, m, nslices, G;
+    // Near-threshold recompute (V update of the paper: the prox returns zero when
+    // mu w d >= rho ||b||): an edge whose two sides differ by at most
+    // delta_fuse * rho ||b|| has ||b_ij|| recomputed in double from the rows of
+    // A_m before the decision; 0 disables it.
+    double delta_fuse;
+    // Feature-sharded iteration: when ext_part is set, the reduction takes each
+    // edge-sweep position's ||b||^2 and the scalar partials from n_ext shards'
+    // partial vectors (shard s at ext_part + s * ext_len: le*T per-position
+    // doubles, then kNumScalarPartials doubles), summed in shard order, instead
+    // of this problem's per-CTA partials.
+    const double* ext_part;
+    int n_ext;
+    long long ext_len;
+    int n, p, ld, ldw, m, nslices, G;
     int la, le, nslots;         // run lengths of the two sweeps; node-sweep partial slots
     int stream_edges;           // 1: per-entry arrays of the sweeps stay in global memory
 };
@@ -140,6 +154,15 @@ cudaError_t launch_pd_extrapolate(const IterParams<R>& P, R* p1_hi, float* p1_lo
 template <typename R>
 cudaError_t launch_pd_finalize(const IterParams<R>& P, float* U_out, int64_t ld_out, int p, cudaStream_t s);
 size_t pd_slice_smem_bytes(int n, int la, int le, int nslots, bool fp64, bool prefetch, bool stream);
+// iteration-kernel variant: 0 automatic, 1 double-buffered staging where it fits, 2 single buffer
+template <typename R>
+cudaError_t launch_pd_slice_variant(const IterParams<R>& P, int variant, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pd_iteration_variant(const IterParams<R>& P, int variant, cudaStream_t s);
+// per-position and scalar partials of this problem's CTAs, summed over CTAs in a
+// fixed order into out (le*T + kNumScalarPartials doubles): one shard's share
+template <typename R>
+cudaError_t launch_pd_shard_partials(const IterParams<R>& P, double* out, cudaStream_t s);
 int pd_reduce_blocks(int le);
 
 // data preparation (prep_kernels.cu)

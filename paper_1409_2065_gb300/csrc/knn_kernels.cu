@@ -394,6 +394,7 @@ cudaError_t knn_min_connected_k(const float* Y0f, int n, int p, int ld, int k_ma
         int h = 0;
         if (r == cudaSuccess) r = cudaMemcpyAsync(&h, ncl, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+        if (r == cudaSuccess && h < 0) r = cudaErrorUnknown;   // components did not settle
         *yes = (h == 1);
         ++*probes;
         return r;

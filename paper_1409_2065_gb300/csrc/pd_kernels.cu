@@ -533,45 +533,114 @@ __global__ void __launch_bounds__(kSliceThreads, 1) pd_slice_kernel(IterParams<R
 constexpr int kRedEdges = 32;
 constexpr int kRedGroups = kReduceThreads / kRedEdges;
 
+// Sum of the d_m pieces ||U_y - A_m||^2 + ||V_y - B_m||^2 over G partial rows
+// of stride `stride` (lane-strided, then a shuffle tree; valid in lane 0).  The
+// reduce kernel and the shard-partials kernel both use it, so one shard's
+// total reproduces the unsharded sum exactly.
+__device__ __forceinline__ double dm_sum(const double* ps, int G, long long stride, int lane) {
+    double acc = 0.0;
+    for (int g = lane; g < G; g += 32) acc += ps[(size_t)g * stride + kPsUA] + ps[(size_t)g * stride + kPsVB];
+    return warp_sum(acc);
+}
+
+// Per edge-sweep position: the 8-group strided sum of the per-CTA ||b||^2
+// partials (group q takes CTAs q, q + 8, ...), then the groups in order.
+__device__ __forceinline__ double nb2_group_sum(const float* Pnb, int G, int LE, int pos, int grp) {
+    double s = 0.0;
+    for (int g = grp; g < G; g += kRedGroups) s += (double)Pnb[(size_t)g * LE + pos];
+    return s;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R> P) {
+    constexpr bool FF = std::is_same<R, float>::value;
     PdState* st = P.st;
     if (st->done) return;
     __shared__ double s_d;
     __shared__ double part[kRedGroups][kRedEdges];
+    __shared__ double s_nb[kRedEdges];
+    __shared__ unsigned s_near;
     __shared__ bool s_last;
-    const int G = P.G, m = P.m, tid = threadIdx.x;
+    __shared__ double red[32];
+    const int G = P.G, tid = threadIdx.x;
+    const int LA = P.la * kSliceThreads, LE = P.le * kSliceThreads;
+    const double* ext = P.ext_part;
     if (tid < 32) {
-        // d_m (Eq. 5): lane-strided partial sums, then a fixed shuffle tree
-        double acc = 0.0;
-        for (int g = tid; g < G; g += 32)
-            acc += P.Ps[(size_t)g * kNumScalarPartials + kPsUA] + P.Ps[(size_t)g * kNumScalarPartials + kPsVB];
-        acc = warp_sum(acc);
+        // d_m (Eq. 5): per-CTA partials (or the shards' totals, in shard order)
+        const double acc = ext ? dm_sum(ext + LE, P.n_ext, P.ext_len, tid) : dm_sum(P.Ps, G, kNumScalarPartials, tid);
         if (tid == 0) s_d = sqrt(acc + st->eps);
     }
     // one lane per edge-sweep position pos = k*T + t, the k-th edge of run t
-    const int LA = P.la * kSliceThreads, LE = P.le * kSliceThreads;
     const int lane = tid % kRedEdges, grp = tid / kRedEdges;
     const int pos = blockIdx.x * kRedEdges + lane;
     const int e = pos < LE ? P.eid[pos] : -1;
     double s = 0.0;
-    if (e >= 0)
-        for (int g = grp; g < G; g += kRedGroups) s += (double)P.Pnb[(size_t)g * LE + pos];
+    if (e >= 0) {
+        if (ext) {
+            for (int q = grp; q < P.n_ext; q += kRedGroups) s += ext[(size_t)q * P.ext_len + pos];
+        } else {
+            s = nb2_group_sum(P.Pnb, G, LE, pos, grp);
+        }
+    }
     part[grp][lane] = s;
     __syncthreads();
     const double d = s_d;
+    const double gamma = st->gamma, rho = st->rho;
+    double lhs = 0.0;
+    bool near = false;
     if (grp == 0) {
-        const double gamma = st->gamma, rho = st->rho;
+        double nb = 0.0;
+        if (e >= 0) {
+            double tot = 0.0;
+            for (int g = 0; g < kRedGroups; ++g) tot += part[g][lane];
+            nb = sqrt(tot);
+            lhs = gamma * P.w[e] * d;
+            const double rhs = rho * nb;
+            // the prox's zero test mu w d >= rho ||b|| within the rounding of the
+            // float partial sums: decide it from ||b|| recomputed in double
+            near = P.delta_fuse > 0.0 && rhs > 0.0 && fabs(lhs - rhs) <= P.delta_fuse * rhs;
+        }
+        s_nb[lane] = nb;
+        const unsigned nm = __ballot_sync(0xffffffffu, near);
+        if (lane == 0) s_near = nm;
+    }
+    __syncthreads();
+    // FP64 recompute of ||a_i - a_j|| from the rows of A_m (written by this
+    // iteration's slice kernel into the slots the next iteration reads), the
+    // whole block on one edge at a time in lane order: fixed-order sums
+    unsigned nm = s_near;
+    if (nm) {
+        const int po = st->par ^ 1;
+        const R* __restrict__ hi = P.Ahi[po];
+        const float* __restrict__ lo = P.Alo[po];
+        while (nm) {
+            const int l = __ffs(nm) - 1;
+            nm &= nm - 1;
+            const int ee = P.eid[blockIdx.x * kRedEdges + l];
+            const size_t oi = (size_t)P.ei[ee] * P.ld, oj = (size_t)P.ej[ee] * P.ld;
+            double acc = 0.0;
+            for (int c = tid; c < P.p; c += kReduceThreads) {
+                double ai = (double)hi[oi + c], aj = (double)hi[oj + c];
+                if constexpr (FF) {
+                    ai += (double)lo[oi + c];
+                    aj += (double)lo[oj + c];
+                }
+                const double dd = ai - aj;
+                acc = fma(dd, dd, acc);
+            }
+            const double tot = block_sum(acc, red);
+            if (tid == 0) s_nb[l] = sqrt(tot);
+            __syncthreads();
+        }
+    }
+    if (grp == 0) {
         const R* tEin = P.t[st->par] + 2 * (size_t)LA;
         R* tAout = P.t[st->par ^ 1];          // (t_{m+1}, t_m) replaces (t_m, t_{m-1})
         R* tEout = tAout + 2 * (size_t)LA;
         bool fz = false;
         unsigned long long h = 0ULL;
         if (e >= 0) {
-            double tot = 0.0;
-            for (int g = 0; g < kRedGroups; ++g) tot += part[g][lane];
-            const double nb = sqrt(tot);
-            const double lhs = gamma * P.w[e] * d;
+            const double nb = s_nb[lane];
             const double rhs = rho * nb;
             fz = lhs >= rhs;                 // the prox returns exactly zero
             const R tnew = fz ? (R)1 : (R)(lhs / rhs);
@@ -594,8 +663,9 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
         if (lane == 0) {
-            P.Rf[2 * blockIdx.x] = (unsigned long long)__popc(ballot);
-            P.Rf[2 * blockIdx.x + 1] = h;
+            P.Rf[3 * blockIdx.x] = (unsigned long long)__popc(ballot);
+            P.Rf[3 * blockIdx.x + 1] = h;
+            P.Rf[3 * blockIdx.x + 2] = (unsigned long long)__popc(s_near);
             __threadfence();
             const unsigned int ticket = atomicAdd(&st->counter, 1u);
             s_last = (ticket == gridDim.x - 1);
@@ -606,28 +676,33 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     __threadfence();
 
     // ---- last block: scalar state update (block-parallel fixed-order sums, then thread 0)
-    const double rho = st->rho;
-    unsigned long long nf_l = 0ULL, hash_l = 0ULL;
+    unsigned long long nf_l = 0ULL, hash_l = 0ULL, nr_l = 0ULL;
     for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
-        nf_l += P.Rf[2 * b];
-        hash_l += P.Rf[2 * b + 1];
+        nf_l += P.Rf[3 * b];
+        hash_l += P.Rf[3 * b + 1];
+        nr_l += P.Rf[3 * b + 2];
     }
     double q_rs = 0.0, q_st = 0.0, q_na = 0.0, q_nz = 0.0, q_dl = 0.0;
-    for (int g = tid; g < G; g += blockDim.x) {
-        const double* ps = P.Ps + (size_t)g * kNumScalarPartials;
-        q_rs += ps[kPsRestart];
-        q_st += ps[kPsStep];
-        q_na += ps[kPsNormA];
-        q_nz += ps[kPsNoise];
-        q_dl += ps[kPsDelta];
+    {
+        const double* base = ext ? ext + LE : P.Ps;
+        const long long stride = ext ? P.ext_len : kNumScalarPartials;
+        const int rows = ext ? P.n_ext : G;
+        for (int g = tid; g < rows; g += blockDim.x) {
+            const double* ps = base + (size_t)g * stride;
+            q_rs += ps[kPsRestart];
+            q_st += ps[kPsStep];
+            q_na += ps[kPsNormA];
+            q_nz += ps[kPsNoise];
+            q_dl += ps[kPsDelta];
+        }
     }
-    __shared__ double red[32];
     const double rs = block_sum(q_rs, red);
     const double stp = block_sum(q_st, red);
     const double na = block_sum(q_na, red);
     const double nzs = block_sum(q_nz, red);
     const double dls = block_sum(q_dl, red);
     const unsigned long long nf = (unsigned long long)block_sum((double)nf_l, red);
+    const unsigned long long nrec = (unsigned long long)block_sum((double)nr_l, red);
     __shared__ unsigned long long hsh[kReduceThreads];
     hsh[tid] = hash_l;
     __syncthreads();
@@ -637,6 +712,8 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     const double unit = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     const double noise = unit * sqrt(nzs);
     st->iter += 1;
+    st->n_recomputed = (int)nrec;
+    st->recompute_total += (long long)nrec;
     st->d_last = d;
     st->alpha2 = st->alpha1;
     st->alpha1 = d / (d + rho);
@@ -724,6 +801,48 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     st->counter = 0u;
 }
 
+
+// One shard's partials of the iteration: per edge-sweep position the ||b||^2
+// partials of its G CTAs summed as pd_reduce_kernel sums them (8 strided
+// groups, then the groups in order), and the scalar partials summed as that
+// kernel's d_m and last block sum them.  With one shard the reduction over
+// these totals is therefore bit-identical to the unsharded one.
+template <typename R>
+__global__ void __launch_bounds__(kReduceThreads) pd_shard_partials_kernel(IterParams<R> P, double* __restrict__ out) {
+    if (P.st->done) return;
+    const int G = P.G, tid = threadIdx.x, LE = P.le * kSliceThreads;
+    __shared__ double part[kRedGroups][kRedEdges];
+    __shared__ double red[32];
+    const int lane = tid % kRedEdges, grp = tid / kRedEdges;
+    const int pos = blockIdx.x * kRedEdges + lane;
+    if (blockIdx.x * kRedEdges < LE) {
+        part[grp][lane] = pos < LE ? nb2_group_sum(P.Pnb, G, LE, pos, grp) : 0.0;
+        __syncthreads();
+        if (grp == 0 && pos < LE) {
+            double tot = 0.0;
+            for (int g = 0; g < kRedGroups; ++g) tot += part[g][lane];
+            out[pos] = tot;
+        }
+        return;
+    }
+    // the extra last block: scalar partials
+    if (tid < 32) {
+        const double acc = dm_sum(P.Ps, G, kNumScalarPartials, tid);
+        if (tid == 0) {
+            out[LE + kPsUA] = acc;   // the two d_m pieces travel as one sum
+            out[LE + kPsVB] = 0.0;
+        }
+    }
+    const int slots[5] = {kPsRestart, kPsStep, kPsNormA, kPsNoise, kPsDelta};
+    for (int k = 0; k < 5; ++k) {
+        double q = 0.0;
+        for (int g = tid; g < G; g += blockDim.x) q += P.Ps[(size_t)g * kNumScalarPartials + slots[k]];
+        const double t = block_sum(q, red);
+        if (tid == 0) out[LE + slots[k]] = t;
+    }
+    if (tid == 0) out[LE + 7] = 0.0;
+}
+
 // ------------------------------------------------------------------ init / begin / finalize
 template <typename R>
 __global__ void pd_init_kernel(IterParams<R> P, const R* Y0, size_t total) {
@@ -765,6 +884,8 @@ __global__ void pd_init_kernel(IterParams<R> P, const R* Y0, size_t total) {
         st->fused_stable = 0;
         st->counter = 0u;
         st->d_last = 0.0;
+        st->n_recomputed = 0;
+        st->recompute_total = 0;
     }
 }
 
@@ -794,6 +915,8 @@ __global__ void pd_begin_gamma_kernel(PdState* st, double gamma, double rho, dou
     for (int q = 0; q < kRateWindows; ++q) st->ring[q] = 0.0;
     st->dmax = 0.0;
     st->counter = 0u;
+    st->n_recomputed = 0;
+    st->recompute_total = 0;
 }
 
 template <typename R>
@@ -862,20 +985,34 @@ static size_t slice_smem_limit() {
 }
 
 template <typename R>
-cudaError_t launch_pd_slice(const IterParams<R>& P, cudaStream_t s) {
+cudaError_t launch_pd_slice_variant(const IterParams<R>& P, int variant, cudaStream_t s) {
     constexpr bool fp64 = std::is_same<R, double>::value;
     count_launches(1);
     // the double buffer is worth it only while at least ~96 KB of the SM's
     // 256 KB L1/shared array stays L1 for the per-edge weights and row loads
+    // (variant 1 takes it whenever it fits; variant 2 never)
     const size_t lim = slice_smem_limit();
     if (P.stream_edges)
         return launch_slice<R, false, true>(P, pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false, true), s);
     const size_t with_pref = pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, true, false);
-    if (with_pref <= lim && with_pref <= kPrefetchSmemMax) return launch_slice<R, true, false>(P, with_pref, s);
+    const size_t pref_cap = variant == 1 ? lim : kPrefetchSmemMax;
+    if (variant != 2 && with_pref <= lim && with_pref <= pref_cap) return launch_slice<R, true, false>(P, with_pref, s);
     const size_t staged = pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false, false);
     if (staged <= lim) return launch_slice<R, false, false>(P, staged, s);
     // edge set too large to stage beside the rows: indices and accumulators stay in global memory
     return launch_slice<R, false, true>(P, pd_slice_smem_bytes(P.n, P.la, P.le, P.nslots, fp64, false, true), s);
+}
+
+template <typename R>
+cudaError_t launch_pd_slice(const IterParams<R>& P, cudaStream_t s) {
+    return launch_pd_slice_variant<R>(P, 0, s);
+}
+
+template <typename R>
+cudaError_t launch_pd_shard_partials(const IterParams<R>& P, double* out, cudaStream_t s) {
+    count_launches(1);
+    pd_shard_partials_kernel<R><<<pd_reduce_blocks(P.le) + 1, kReduceThreads, 0, s>>>(P, out);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -886,10 +1023,15 @@ cudaError_t launch_pd_reduce(const IterParams<R>& P, cudaStream_t s) {
 }
 
 template <typename R>
-cudaError_t launch_pd_iteration(const IterParams<R>& P, cudaStream_t s) {
-    cudaError_t e = launch_pd_slice<R>(P, s);
+cudaError_t launch_pd_iteration_variant(const IterParams<R>& P, int variant, cudaStream_t s) {
+    cudaError_t e = launch_pd_slice_variant<R>(P, variant, s);
     if (e != cudaSuccess) return e;
     return launch_pd_reduce<R>(P, s);
+}
+
+template <typename R>
+cudaError_t launch_pd_iteration(const IterParams<R>& P, cudaStream_t s) {
+    return launch_pd_iteration_variant<R>(P, 0, s);
 }
 
 template <typename R>
@@ -979,6 +1121,12 @@ cudaError_t launch_pd_finalize(const IterParams<R>& P, float* U_out, int64_t ld_
 }
 
 template cudaError_t launch_pd_iteration<float>(const IterParams<float>&, cudaStream_t);
+template cudaError_t launch_pd_iteration_variant<float>(const IterParams<float>&, int, cudaStream_t);
+template cudaError_t launch_pd_iteration_variant<double>(const IterParams<double>&, int, cudaStream_t);
+template cudaError_t launch_pd_slice_variant<float>(const IterParams<float>&, int, cudaStream_t);
+template cudaError_t launch_pd_slice_variant<double>(const IterParams<double>&, int, cudaStream_t);
+template cudaError_t launch_pd_shard_partials<float>(const IterParams<float>&, double*, cudaStream_t);
+template cudaError_t launch_pd_shard_partials<double>(const IterParams<double>&, double*, cudaStream_t);
 template cudaError_t launch_pd_slice<float>(const IterParams<float>&, cudaStream_t);
 template cudaError_t launch_pd_slice<double>(const IterParams<double>&, cudaStream_t);
 template cudaError_t launch_pd_reduce<float>(const IterParams<float>&, cudaStream_t);
