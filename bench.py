@@ -252,6 +252,10 @@ def batch_specs(count, nmax, pmax, seed=3):
 
 
 def run_batch(args, ccx, torch, rank):
+    """Batched workload: the same problems solved (1) one call after another (the plain
+    per-launch path), (2) together with ccx_solve_batch on the default grid (results
+    must be bit-identical to (1)), (3) together after ccx_tune_grid picked each
+    problem's grid (results agree with (1) within the FP32 parity bar)."""
     Xs = batch_specs(args.batch, args.batch_nmax, args.batch_pmax)
 
     def make():
@@ -264,38 +268,65 @@ def run_batch(args, ccx, torch, rank):
 
     probs = make()
     grids = [synth.log_grid(0.03 * pr.fusion_scale(), 3.0 * pr.fusion_scale(), args.batch_gammas) for pr in probs]
-    # one call per problem, one after another
+    # (1) one call per problem, one after another
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     seq = [pr.solve_path(g, device=True) for pr, g in zip(probs, grids)]
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     iters = sum(s["iters"] for r in seq for s in r[2])
+    conv_seq = all(s["converged"] in (1, 2) for r in seq for s in r[2])
+    # (2) together, default grid
     for pr in probs:
         pr.reset_path()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Us, Ls, stats, status, _ = ccx.solve_batch(probs, grids, device=True, max_active=args.batch)
+    Us, Ls, stats, status, _ = ccx.solve_batch(probs, grids, device=True, max_active=args.batch_active)
     torch.cuda.synchronize()
     t_bat = time.perf_counter() - t0
     same = all(torch.equal(Us[i], seq[i][0]) and torch.equal(Ls[i], seq[i][1]) for i in range(len(probs)))
+    del Us, Ls
+    # (3) together, grids from the autotuner
+    for pr in probs:
+        pr.reset_path()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g_min = max(1, 152 // max(1, args.batch_active))
+    tuned = [pr.tune_grid(g_min)[0] for pr in probs]
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Ut, Lt, stt, status_t, _ = ccx.solve_batch(probs, grids, device=True, max_active=args.batch_active)
+    torch.cuda.synchronize()
+    t_tb = time.perf_counter() - t0
+    rel = max(float(torch.linalg.vector_norm(Ut[i][g] - seq[i][0][g]) / torch.linalg.vector_norm(seq[i][0][g]))
+              for i in range(len(probs)) for g in range(len(grids[i])))
+    lab_same = sum(int(torch.equal(Lt[i], seq[i][1])) for i in range(len(probs)))
+    conv_t = all(s["converged"] in (1, 2) for st_ in stt for s in st_)
     sz = [X.shape for X in Xs]
     line = {"metric": "gamma-path solves/s", "workload": f"{args.batch} problems, n~U[50,{args.batch_nmax}], "
             f"p~U[10,{args.batch_pmax}], 2-8 clusters, kNN k=10, {args.batch_gammas} gammas in [0.03,3]*gamma0",
-            "sequential": len(probs) / t_seq, "batched": len(probs) / t_bat, "speedup": t_seq / t_bat,
-            "seconds_sequential": t_seq, "seconds_batched": t_bat, "mm_iterations": int(iters),
-            "sum_np": int(sum(n * p for n, p in sz)), "identical_results": bool(same), "dtype": "f32",
-            "data": "synthetic"}
+            "plain_one_call_per_problem": len(probs) / t_seq, "batched": len(probs) / t_bat,
+            "batched_tuned_grids": len(probs) / (t_tb + t_tune),
+            "speedup": t_seq / t_bat, "speedup_tuned_incl_tuning": t_seq / (t_tb + t_tune),
+            "seconds_plain": t_seq, "seconds_batched": t_bat, "seconds_tuned": t_tb, "seconds_tuning": t_tune,
+            "tuned_grids": tuned, "max_active": args.batch_active, "mm_iterations_plain": int(iters),
+            "sum_np": int(sum(n * p for n, p in sz)), "identical_results": bool(same),
+            "tuned_max_rel_diff_U": rel, "tuned_problems_with_identical_labels": lab_same,
+            "all_converged": bool(conv_seq and conv_t and all(s == 0 for s in status + status_t)),
+            "dtype": "f32", "data": "synthetic"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def run_serve(args, ccx, torch, rank):
+    """Serving workload: Poisson arrivals of jobs from the batched size distribution at each
+    rate of --serve, served by ccx_server with continuous batching and, on the same jobs and
+    arrival times, one job at a time (max_active = 1); p50/p99 latency and solves/s."""
+    rates = [float(r) for r in str(args.serve).split(",")]
     Xs = batch_specs(args.serve_jobs, args.batch_nmax, args.batch_pmax, seed=4)
-    rng = np.random.default_rng(4)
-    gaps = rng.exponential(1.0 / args.serve, size=len(Xs))
 
-    def arm(max_active):
+    def arm(max_active, gaps):
         probs = []
         for X in Xs:
             pr = ccx.Problem(torch.from_numpy(X).cuda())
@@ -306,11 +337,13 @@ def run_serve(args, ccx, torch, rank):
         torch.cuda.synchronize()
         srv = ccx.Server(max_active=max_active)
         arrive, done, results = [0.0] * len(Xs), [0.0] * len(Xs), [None] * len(Xs)
+        codes = [None] * len(Xs)
 
         def waiter(i, t):
             st, U, L, stats = srv.wait(t, -1)
             done[i] = time.perf_counter()
             results[i] = (U, L)
+            codes[i] = st
 
         threads = []
         t0 = time.perf_counter()
@@ -330,17 +363,23 @@ def run_serve(args, ccx, torch, rank):
         q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
         for pr in probs:
             pr.close()
-        return {"p50_s": q(0.5), "p99_s": q(0.99), "solves_per_s": len(Xs) / wall, "wall_s": wall}, results
+        return {"p50_s": q(0.5), "p99_s": q(0.99), "solves_per_s": len(Xs) / wall, "wall_s": wall,
+                "all_ok": all(c == 0 for c in codes)}, results
 
-    served, r1 = arm(32)
-    plain, r2 = arm(1)
-    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(r1, r2))
-    line = {"metric": "served gamma-path solves/s and latency", "rate_jobs_per_s": args.serve,
-            "workload": f"{len(Xs)} jobs, Poisson arrivals, n~U[50,{args.batch_nmax}], p~U[10,{args.batch_pmax}], "
-                        f"2-8 clusters, kNN k=10, {args.batch_gammas} gammas in [0.03,3]*gamma0",
-            "continuous_batching": served, "one_at_a_time": plain,
-            "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"],
-            "identical_results": bool(same), "dtype": "f32", "data": "synthetic"}
+    per_rate = []
+    for r_i, rate in enumerate(rates):
+        gaps = np.random.default_rng(4 + r_i).exponential(1.0 / rate, size=len(Xs))
+        served, r1 = arm(args.serve_active, gaps)
+        plain, r2 = arm(1, gaps)
+        same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(r1, r2))
+        per_rate.append({"rate_jobs_per_s": rate, "continuous_batching": served, "one_at_a_time": plain,
+                         "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"],
+                         "identical_results": bool(same)})
+    line = {"metric": "served gamma-path solves/s and latency",
+            "workload": f"{len(Xs)} jobs per rate, Poisson arrivals, n~U[50,{args.batch_nmax}], "
+                        f"p~U[10,{args.batch_pmax}], 2-8 clusters, kNN k=10, {args.batch_gammas} gammas in "
+                        "[0.03,3]*gamma0", "max_active": args.serve_active, "rates": per_rate,
+            "dtype": "f32", "data": "synthetic"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -360,14 +399,17 @@ def main():
                     help="instead of the default step: P independent problems from the batched-workload size "
                          "distribution (scaled by --batch-nmax/--batch-pmax), solved one call after another and "
                          "then together with ccx_solve_batch; prints the two solve rates")
-    ap.add_argument("--serve", type=float, default=0.0, metavar="RATE",
-                    help="instead of the default step: Poisson arrivals of --serve-jobs jobs at RATE jobs/s "
-                         "(sizes as --batch), served by ccx_server with continuous batching and, for comparison, "
-                         "one job at a time; prints p50/p99 latency and solve rates")
+    ap.add_argument("--serve", type=str, default="", metavar="RATES",
+                    help="instead of the default step: for each comma-separated rate, Poisson arrivals of "
+                         "--serve-jobs jobs at that many jobs/s (sizes as --batch), served by ccx_server with "
+                         "continuous batching and, for comparison, one job at a time; prints p50/p99 latency "
+                         "and solve rates")
     ap.add_argument("--serve-jobs", type=int, default=64)
+    ap.add_argument("--serve-active", type=int, default=32, help="jobs the server runs at once")
     ap.add_argument("--batch-nmax", type=int, default=2000)
     ap.add_argument("--batch-pmax", type=int, default=5000)
     ap.add_argument("--batch-gammas", type=int, default=30)
+    ap.add_argument("--batch-active", type=int, default=32, help="problems with work queued at once")
     ap.add_argument("--min-k", type=int, default=0, metavar="KMAX",
                     help="instead of the default step: time the search for the smallest k <= KMAX whose kNN "
                          "graph of the workload is connected, on the GPU and with the oracle")
@@ -378,6 +420,9 @@ def main():
     ap.add_argument("--pc", type=int, default=0, metavar="Q",
                     help="instead of the default step: time the Q principal axes of the workload on the GPU and "
                          "with the oracle, and the projected path against the full path through host buffers")
+    ap.add_argument("--gram-compare", action="store_true",
+                    help="instead of the default step: time the kNN weights of the workload with the Gram on "
+                         "TF32 and BF16 tensor cores and on FP32 CUDA cores, and check the edge sets agree")
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -395,7 +440,7 @@ def main():
     if args.batch:
         run_batch(args, ccx, torch, rank)
         return
-    if args.serve > 0:
+    if args.serve:
         run_serve(args, ccx, torch, rank)
         return
     W = workload(args.workload)
@@ -465,6 +510,27 @@ def main():
                           "bytes_out_per_gamma_full": int(n * p * 4), "bytes_out_per_gamma_projected": int(n * args.pc * 4)}),
               flush=True)
         return
+    if args.gram_compare:
+        out = {}
+        edges0 = None
+        for gram, name in ((0, "tf32_tensor_cores"), (1, "bf16_tensor_cores"), (2, "fp32_cuda_cores")):
+            kw = dict(phi=W.get("phi", 0.0), phi_auto=W.get("phi_auto", False), normalize=W["normalize"], gram=gram)
+            pr.build_knn(W["k"], **kw)                       # warm-up
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                pr.build_knn(W["k"], **kw)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            e = pr.get_edges()
+            if edges0 is None:
+                edges0 = e
+            same = all(np.array_equal(a, b) for a, b in zip(e, edges0))
+            out[name] = {"seconds_median": statistics.median(ts), "edges_identical_to_tf32": bool(same)}
+        print(json.dumps({"metric": "seconds per kNN weight build by Gram precision", "workload": W["desc"],
+                          "edges": int(edges0[0].size), **out}), flush=True)
+        return
     if args.min_k:
         pr.min_connected_k(args.min_k)                      # warm-up
         torch.cuda.synchronize()
@@ -518,6 +584,7 @@ def main():
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
             iters.append(sum(s["iters"] for s in stats))
+            per_gamma = [(int(s["iters"]), int(s["converged"]), int(s["n_fused"])) for s in stats]
     launches = ccx.kernel_launches() - l0
     if dist:
         dist.barrier()
@@ -592,6 +659,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": run_config(W, m, ws),
                 "iters_per_step": int(statistics.median(iters)),
+                "per_gamma_iters_converged_fused": per_gamma,
                 "solves_per_s": ws / t_max,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_note,

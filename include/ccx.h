@@ -80,6 +80,11 @@ typedef struct {
     double phi;     /* >= 0, used when phi_auto == 0 */
     int phi_auto;
     int normalize;
+    int gram;       /* Gram matrix that selects the candidate neighbours: 0 (default) tensor cores on
+                       TF32 operands, 1 tensor cores on BF16 operands (rounded to nearest), 2 FP32 CUDA
+                       cores.  Candidates are chosen with a rigorous bound on that Gram's error and get
+                       exact distances, so the edge set is the same for every choice; a coarser Gram only
+                       gives more candidates to refine.  Unused when k >= n - 1 (all pairs). */
 } ccx_knn_rule;
 
 /*
@@ -155,6 +160,26 @@ void ccx_opts_default(ccx_opts* o);
  */
 ccx_status ccx_problem_create(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld,
                               int precision, void* stream, ccx_problem** out);
+
+/*
+ * Standardise the predictors (Methods: the predictors are standardised before
+ * clustering) on the GPU, using observed entries only: each column is centred
+ * on the mean of its observed entries and divided by their standard deviation
+ * (divisor = their count), in double and rounded once to the working
+ * precision; a column whose observed entries are all equal is centred only,
+ * and one with no observed entry stays 0.  Call it right after
+ * ccx_problem_create: it replaces the problem's data, so it also clears the
+ * edge set, the principal axes and the path state.
+ */
+ccx_status ccx_standardize(ccx_problem* pr);
+
+/*
+ * Copy the start matrix Y_0 out: the data as the solver sees them (after any
+ * ccx_standardize), with each missing entry at its column's observed mean
+ * (Missing Data: the iteration starts from U = Y_0).  Y0_out: n x p floats,
+ * host or device.
+ */
+ccx_status ccx_get_start(const ccx_problem* pr, float* Y0_out);
 
 /*
  * Set the weighted edge set explicitly (host arrays): edge e joins cases
@@ -234,7 +259,10 @@ ccx_status ccx_fusion_scale(const ccx_problem* pr, double* gamma0);
  *             handles it).
  *   Set-up  : the first call on a device looks up the buffer's address on
  *             that device and keeps it; make that first call before any
- *             stream capture begins on the device.
+ *             stream capture begins on the device.  The kept address belongs
+ *             to the device's current context: after cudaDeviceReset (or any
+ *             teardown of the primary context) it is no longer valid, and
+ *             this call must not be used again in that process.
  *   Sharing : every call in the process uses the same two buffers, which keep
  *             the last call's per-edge ratios.  A call writes every entry it
  *             reads, so nothing has to be cleared first.  Two calls whose GPU
@@ -398,6 +426,21 @@ ccx_status ccx_shard_begin_gamma(ccx_problem* pr, double gamma, const ccx_opts* 
 ccx_status ccx_shard_partials(ccx_problem* pr, double* part, int64_t* len);
 ccx_status ccx_shard_reduce(ccx_problem* pr, const double* parts, int n_shards, int* done);
 ccx_status ccx_shard_end_gamma(ccx_problem* pr, float* U_out, int32_t* labels_out, ccx_gamma_stats* stats);
+
+/*
+ * Autotuning of the iteration kernel's grid (no counterpart in the paper).
+ * Times 16 MM iterations of this problem at grids of G, G/2, G/4, ... CTAs
+ * (G = one per SM, at most one per 4-column slice), down to g_min, and keeps
+ * the grid with the least SM time per iteration (grid x iteration time; a
+ * smaller grid is taken only when it saves at least 2 %).  Later solves of the
+ * problem whose options leave max_ctas at 0 use that grid, so a small problem
+ * leaves SMs to the others in ccx_solve_batch or a server; results agree with
+ * the default grid within the rounding of the per-CTA partial sums.  Needs the
+ * edge set; must be called before the first solve or after ccx_reset_path (it
+ * runs iterations from Y_0 and then resets the path).
+ *   g_out : the chosen grid.  ms_out: NULL, or its mean milliseconds per iteration.
+ */
+ccx_status ccx_tune_grid(ccx_problem* pr, int g_min, int* g_out, double* ms_out);
 
 /* Forget the warm-start state: the next ccx_solve_path starts from Y_0, V = 0. */
 ccx_status ccx_reset_path(ccx_problem* pr);

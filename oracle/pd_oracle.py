@@ -52,6 +52,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 __all__ = [
+    "standardize",
     "principal_axes",
     "project_path",
     "geo_distance",
@@ -123,6 +124,29 @@ class EdgeGraph:
 # ----------------------------------------------------------------------------
 # Data preparation and constants
 # ----------------------------------------------------------------------------
+def standardize(X: np.ndarray, mask) -> np.ndarray:
+    """Standardised predictors (Methods: the predictors are standardised before
+    clustering), using observed entries only: each column is centred on the
+    mean of its observed entries and divided by their standard deviation
+    (divisor = the number of observed entries); a column whose observed
+    entries are all equal is centred only, and a column with no observed
+    entry is left at 0.  Missing entries are returned as 0 (their value is
+    never data).  FP64 throughout."""
+    X = np.asarray(X, dtype=np.float64)
+    n, p = X.shape
+    obs = np.ones((n, p), bool) if mask is None else np.asarray(mask).astype(bool)
+    out = np.zeros((n, p))
+    for c in range(p):
+        vals = X[obs[:, c], c]
+        if vals.size == 0:
+            continue
+        mean = vals.sum() / vals.size
+        dev = vals - mean
+        sd = np.sqrt((dev * dev).sum() / vals.size)
+        out[obs[:, c], c] = dev / sd if sd > 0 else dev
+    return out
+
+
 def fill_missing(X: np.ndarray, mask) -> np.ndarray:
     """Y_0: X with each missing entry replaced by its column's observed mean (0 if none)."""
     X = np.asarray(X, dtype=np.float64)

@@ -29,7 +29,8 @@ STATUS = {0: "CCX_OK", 1: "CCX_EINVAL", 2: "CCX_ENOMEM", 3: "CCX_ECUDA", 4: "CCX
 
 
 class KnnRule(C.Structure):
-    _fields_ = [("k", C.c_int), ("phi", C.c_double), ("phi_auto", C.c_int), ("normalize", C.c_int)]
+    _fields_ = [("k", C.c_int), ("phi", C.c_double), ("phi_auto", C.c_int), ("normalize", C.c_int),
+                ("gram", C.c_int)]
 
 
 class Opts(C.Structure):
@@ -54,6 +55,8 @@ _sigs = {
     "ccx_opts_default": (None, [C.POINTER(Opts)]),
     "ccx_problem_create": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_int, _P, C.POINTER(_P)]),
     "ccx_set_edges": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
+    "ccx_standardize": (C.c_int, [_P]),
+    "ccx_get_start": (C.c_int, [_P, _P]),
     "ccx_build_knn": (C.c_int, [_P, C.POINTER(KnnRule)]),
     "ccx_get_edges": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P]),
     "ccx_min_connected_k": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
@@ -74,6 +77,7 @@ _sigs = {
     "ccx_shard_partials": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
     "ccx_shard_reduce": (C.c_int, [_P, _P, C.c_int, C.POINTER(C.c_int)]),
     "ccx_shard_end_gamma": (C.c_int, [_P, _P, _P, C.POINTER(GammaStats)]),
+    "ccx_tune_grid": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "ccx_reset_path": (C.c_int, [_P]),
     "ccx_problem_destroy": (C.c_int, [_P]),
     "ccx_time_iterations": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
@@ -150,6 +154,18 @@ def problem_create(X, mask=None, precision=CCX_FP32, stream=None):
     return h.value
 
 
+def standardize(h) -> None:
+    """Standardise the problem's columns on their observed entries (ccx_standardize)."""
+    _check(_lib.ccx_standardize(h))
+
+
+def get_start(h, n: int, p: int):
+    """Y_0 as the solver sees it (n x p float32)."""
+    Y = np.empty((n, p), np.float32)
+    _check(_lib.ccx_get_start(h, Y.ctypes.data))
+    return Y
+
+
 def problem_destroy(h) -> None:
     _check(_lib.ccx_problem_destroy(h))
 
@@ -161,15 +177,16 @@ def set_edges(h, ei, ej, w) -> None:
     _check(_lib.ccx_set_edges(h, ei.size, ei.ctypes.data, ej.ctypes.data, w.ctypes.data))
 
 
-def build_knn(h, k: int, phi: float = 0.0, phi_auto: bool = False, normalize: bool = False) -> None:
-    r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)))
+def build_knn(h, k: int, phi: float = 0.0, phi_auto: bool = False, normalize: bool = False, gram: int = 0) -> None:
+    """kNN Gaussian-kernel weights; gram: 0 TF32 tensor cores, 1 BF16 tensor cores, 2 FP32 CUDA cores."""
+    r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)), int(gram))
     _check(_lib.ccx_build_knn(h, C.byref(r)))
 
 
 def build_knn_composite(h, k: int, coords, alpha: float, phi: float = 0.0, phi_auto: bool = False,
                         normalize: bool = False, geodesic: bool = False) -> None:
     """kNN weights on alpha * genetic + (1 - alpha) * geographic distance; coords: n x 2 (lat, lon) degrees."""
-    r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)))
+    r = KnnRule(int(k), float(phi), int(bool(phi_auto)), int(bool(normalize)), 0)
     c = np.ascontiguousarray(coords, dtype=np.float64)
     _check(_lib.ccx_build_knn_composite(h, C.byref(r), c.ctypes.data, float(alpha), int(bool(geodesic))))
 
@@ -471,6 +488,13 @@ def reset_path(h) -> None:
     _check(_lib.ccx_reset_path(h))
 
 
+def tune_grid(h, g_min: int = 1):
+    """(grid, ms per iteration) chosen by ccx_tune_grid for this problem."""
+    g, ms = C.c_int(0), C.c_double(0.0)
+    _check(_lib.ccx_tune_grid(h, int(g_min), C.byref(g), C.byref(ms)))
+    return g.value, ms.value
+
+
 def time_iterations(h, gamma: float, n_iter: int, opts: Opts | None = None):
     """(mean ms of the fused iteration kernel, mean ms of the reduction kernel) over n_iter iterations."""
     a, b = C.c_double(0.0), C.c_double(0.0)
@@ -503,15 +527,20 @@ def kernel_launches() -> int:
 class Problem:
     """Owning wrapper around a problem handle."""
 
-    def __init__(self, X, mask=None, precision=CCX_FP32, stream=None):
+    def __init__(self, X, mask=None, precision=CCX_FP32, stream=None, standardize=False):
         self.n, self.p = int(X.shape[0]), int(X.shape[1])
         self.h = problem_create(X, mask, precision, stream)
+        if standardize:
+            globals()["standardize"](self.h)
+
+    def get_start(self):
+        return get_start(self.h, self.n, self.p)
 
     def set_edges(self, ei, ej, w):
         set_edges(self.h, ei, ej, w)
 
-    def build_knn(self, k, phi=0.0, phi_auto=False, normalize=False):
-        build_knn(self.h, k, phi, phi_auto, normalize)
+    def build_knn(self, k, phi=0.0, phi_auto=False, normalize=False, gram=0):
+        build_knn(self.h, k, phi, phi_auto, normalize, gram)
 
     def get_edges(self):
         return get_edges(self.h)
@@ -536,6 +565,9 @@ class Problem:
 
     def reset_path(self):
         reset_path(self.h)
+
+    def tune_grid(self, g_min=1):
+        return tune_grid(self.h, g_min)
 
     def time_iterations(self, gamma, n_iter, opts=None):
         return time_iterations(self.h, gamma, n_iter, opts)

@@ -83,6 +83,7 @@ cudaError_t dalloc(T** p, size_t count) {
 
 namespace {
 struct ShardState;
+void drop_shard(ccx_problem* pr);
 }  // namespace
 
 struct ccx_problem {
@@ -163,6 +164,7 @@ struct ccx_problem {
     int stream_edges = 0;        // from the options of the current call
     int variant = 0;
     int max_ctas = 0;
+    int tuned_G = 0;             // grid chosen by ccx_tune_grid (0: none), used when the options set no cap
     double delta_fuse = 1e-5;
 };
 
@@ -606,19 +608,21 @@ ccx_status check_limits(ccx_problem* pr) {
     return CCX_OK;
 }
 
-// grid of the iteration kernel: one CTA per SM, at most one per slice, capped by max_ctas
-int grid_of(const ccx_problem* pr) {
+// grid of the iteration kernel: one CTA per SM, at most one per slice, capped by `cap` (> 0)
+int grid_of_cap(const ccx_problem* pr, int cap) {
     const int nsl = (int)((pr->p + kSliceCols - 1) / kSliceCols);
     int G = std::min(nsl, pr->num_sms);
-    if (pr->max_ctas > 0) G = std::min(G, pr->max_ctas);
+    if (cap > 0) G = std::min(G, cap);
     return std::max(G, 1);
 }
+
+int grid_of(const ccx_problem* pr) { return grid_of_cap(pr, pr->max_ctas); }
 
 // The options of a call that shape the iteration kernel's launch.
 void apply_opts(ccx_problem* pr, const ccx_opts& o) {
     pr->stream_edges = o.stream_edges ? 1 : 0;
     pr->variant = o.slice_variant;
-    pr->max_ctas = o.max_ctas;
+    pr->max_ctas = o.max_ctas > 0 ? o.max_ctas : pr->tuned_G;
     pr->delta_fuse = o.fuse_delta;
 }
 
@@ -961,6 +965,24 @@ ccx_status path_close(PathRun& r, ccx_status run_status) {
     return CCX_OK;
 }
 
+// Y_0 (missing entries at observed column means), its column means and the
+// norms ||Y_c||_F and ||Y_0||_F that fix rho, eps and the error floor.
+ccx_status prepare_start(ccx_problem* pr) {
+    const int64_t n = pr->n, p = pr->p;
+    CUDA_TRY(launch_fill_missing(pr->Xf, pr->Xd, pr->maskbits, (int)n, (int)p, pr->ld, pr->ldw, pr->colmean,
+                                 pr->Y0f, pr->Y0d, pr->d_ss, pr->work));
+    double ss = 0.0;
+    std::vector<double> cm(p);
+    CUDA_TRY(cudaMemcpyAsync(&ss, pr->d_ss, sizeof(double), cudaMemcpyDeviceToHost, pr->work));
+    CUDA_TRY(cudaMemcpyAsync(cm.data(), pr->colmean, sizeof(double) * p, cudaMemcpyDeviceToHost, pr->work));
+    CUDA_TRY(cudaStreamSynchronize(pr->work));
+    pr->nyc = std::sqrt(ss);
+    double s0 = 0.0;
+    for (int64_t c = 0; c < p; ++c) s0 += cm[c] * cm[c];
+    pr->ny0 = std::sqrt(ss + (double)n * s0);   // ||Y_0||^2 = ||Y_c||^2 + n ||mean||^2
+    return CCX_OK;
+}
+
 // Options of one solve, validated; the FP64 default tolerance is tighter.
 ccx_status resolve_opts(const ccx_problem* pr, const ccx_opts* opts, ccx_opts* o) {
     ccx_opts_default(o);
@@ -1077,25 +1099,17 @@ ccx_status ccx_problem_create(const float* X, const uint8_t* mask, int64_t n, in
     TRY(dalloc(&bad, 2));
     TRY(cudaMemsetAsync(bad, 0, 2 * sizeof(int), pr->work));
     TRY(launch_pack_input(Xsrc, Msrc, n, p, ld, pr->Xf, pr->Xd, pr->maskbits, pr->ld, pr->ldw, bad, pr->work));
-    TRY(launch_fill_missing(pr->Xf, pr->Xd, pr->maskbits, (int)n, (int)p, pr->ld, pr->ldw, pr->colmean, pr->Y0f,
-                            pr->Y0d, pr->d_ss, pr->work));
     int hbad[2] = {0, 0};
-    double ss = 0.0;
     TRY(cudaMemcpyAsync(hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, pr->work));
-    TRY(cudaMemcpyAsync(&ss, pr->d_ss, sizeof(double), cudaMemcpyDeviceToHost, pr->work));
     TRY(cudaStreamSynchronize(pr->work));
     cudaFree(Xtmp);
     cudaFree(Mtmp);
     cudaFree(bad);
     if (hbad[0] > 0) return bail(fail(CCX_EINVAL, "%d observed entries of X are not finite", hbad[0]));
     if (hbad[1] > 0) return bail(fail(CCX_EINVAL, "%d rows have no observed entry", hbad[1]));
-    pr->nyc = std::sqrt(ss);
     {
-        std::vector<double> cm(p);
-        TRY(cudaMemcpy(cm.data(), pr->colmean, sizeof(double) * p, cudaMemcpyDeviceToHost));
-        double s0 = 0.0;
-        for (int64_t c = 0; c < p; ++c) s0 += cm[c] * cm[c];
-        pr->ny0 = std::sqrt(ss + (double)n * s0);   // ||Y_0||^2 = ||Y_c||^2 + n ||mean||^2
+        const ccx_status st = prepare_start(pr);
+        if (st != CCX_OK) return bail(st);
     }
     // an empty edge set until the caller sets or builds one
     {
@@ -1107,6 +1121,41 @@ ccx_status ccx_problem_create(const float* X, const uint8_t* mask, int64_t n, in
 #undef TRY
     *out = pr;
     return CCX_OK;
+}
+
+ccx_status ccx_standardize(ccx_problem* pr) {
+    g_err.clear();
+    if (!pr) return fail(CCX_EINVAL, "problem is NULL");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    CUDA_TRY(launch_standardize(pr->Xf, pr->Xd, pr->has_mask ? pr->maskbits : nullptr, (int)pr->n, (int)pr->p, pr->ld,
+                                pr->ldw, pr->colmean, pr->work));
+    s = prepare_start(pr);
+    if (s != CCX_OK) return s;
+    // the data changed: weights, principal axes and the path state no longer apply
+    cudaFree(pr->pc_axes);
+    cudaFree(pr->Sstage);
+    pr->pc_axes = nullptr;
+    pr->Sstage = nullptr;
+    pr->pc_q = 0;
+    std::vector<int> e0;
+    std::vector<double> w0;
+    s = install_edges(pr, e0, e0, w0);
+    if (s != CCX_OK) return s;
+    drop_shard(pr);
+    return leave(pr);
+}
+
+ccx_status ccx_get_start(const ccx_problem* pr_c, float* Y0_out) {
+    g_err.clear();
+    ccx_problem* pr = const_cast<ccx_problem*>(pr_c);
+    if (!pr || !Y0_out) return fail(CCX_EINVAL, "NULL argument");
+    ccx_status s = enter(pr);
+    if (s != CCX_OK) return s;
+    CUDA_TRY(cudaMemcpy2DAsync(Y0_out, sizeof(float) * pr->p, pr->Y0f, sizeof(float) * pr->ld, sizeof(float) * pr->p,
+                               pr->n, is_device_ptr(Y0_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               pr->work));
+    return leave(pr);
 }
 
 ccx_status ccx_set_edges(ccx_problem* pr, int64_t n_edges, const int32_t* ei, const int32_t* ej, const double* w) {
@@ -1126,13 +1175,14 @@ ccx_status ccx_build_knn(ccx_problem* pr, const ccx_knn_rule* rule) {
     if (rule->k < 1) return fail(CCX_EINVAL, "k must be >= 1");
     if (!rule->phi_auto && (!std::isfinite(rule->phi) || rule->phi < 0.0))
         return fail(CCX_EINVAL, "phi must be finite and >= 0");
+    if (rule->gram < 0 || rule->gram > 2) return fail(CCX_EINVAL, "gram must be 0, 1 or 2");
     ccx_status s = enter(pr);
     if (s != CCX_OK) return s;
     knn_set_exact_rows(pr->Xf, pr->has_mask ? pr->maskbits : nullptr, pr->colmean, pr->ldw);
     KnnResult res;
     std::string err;
     cudaError_t e = knn_build(pr->Y0f, (int)pr->n, (int)pr->p, pr->ld, rule->k, rule->phi, rule->phi_auto,
-                              rule->normalize, pr->work, &res, &err);
+                              rule->normalize, pr->work, &res, &err, nullptr, 1.0, 0, rule->gram);
     if (e == cudaErrorNotSupported) return fail(CCX_EUNSUPPORTED, "%s", err.c_str());
     if (e != cudaSuccess) return fail(CCX_ECUDA, "kNN build failed: %s", cudaGetErrorString(e));
     s = install_edges(pr, res.ei, res.ej, res.w);
@@ -1148,6 +1198,7 @@ ccx_status ccx_build_knn_composite(ccx_problem* pr, const ccx_knn_rule* rule, co
     if (!rule->phi_auto && (!std::isfinite(rule->phi) || rule->phi < 0.0))
         return fail(CCX_EINVAL, "phi must be finite and >= 0");
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(CCX_EINVAL, "alpha must be in [0, 1]");
+    if (rule->gram < 0 || rule->gram > 2) return fail(CCX_EINVAL, "gram must be 0, 1 or 2");
     for (int64_t i = 0; i < pr->n; ++i) {
         const double la = coords[2 * i], lo = coords[2 * i + 1];
         if (!std::isfinite(la) || !std::isfinite(lo) || la < -90.0 || la > 90.0)
@@ -1163,7 +1214,7 @@ ccx_status ccx_build_knn_composite(ccx_problem* pr, const ccx_knn_rule* rule, co
     std::string err;
     if (e == cudaSuccess)
         e = knn_build(pr->Y0f, (int)pr->n, (int)pr->p, pr->ld, rule->k, rule->phi, rule->phi_auto, rule->normalize,
-                      pr->work, &res, &err, geo, alpha, geodesic ? 1 : 0);
+                      pr->work, &res, &err, geo, alpha, geodesic ? 1 : 0, rule->gram);
     cudaFree(geo);
     if (e == cudaErrorNotSupported) return fail(CCX_EUNSUPPORTED, "%s", err.c_str());
     if (e != cudaSuccess) return fail(CCX_ECUDA, "kNN build failed: %s", cudaGetErrorString(e));
@@ -1901,17 +1952,15 @@ ccx_status ccx_shard_end_gamma(ccx_problem* pr, float* U_out, int32_t* labels_ou
     return leave(pr);
 }
 
-ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts, double* slice_ms,
-                               double* reduce_ms) {
-    g_err.clear();
-    if (!pr || !slice_ms || !reduce_ms) return fail(CCX_EINVAL, "NULL argument");
-    if (!std::isfinite(gamma) || gamma < 0.0) return fail(CCX_EINVAL, "gamma must be finite and >= 0");
-    if (n_iter < 1) return fail(CCX_EINVAL, "n_iter must be >= 1");
-    ccx_opts o;
-    ccx_status s = resolve_opts(pr, opts, &o);
-    if (s != CCX_OK) return s;
-    apply_opts(pr, o);
-    s = check_limits(pr);
+}  // extern "C"
+
+namespace {
+// n_iter MM iterations of the current warm-start state at penalty gamma with
+// the stopping test off, each kernel launched alone between CUDA events on the
+// work stream; mean milliseconds of the slice and reduce kernels.
+ccx_status time_iterations_impl(ccx_problem* pr, double gamma, int n_iter, const ccx_opts& o, double* slice_ms,
+                                double* reduce_ms) {
+    ccx_status s = check_limits(pr);
     if (s != CCX_OK) return s;
     s = enter(pr);
     if (s != CCX_OK) return s;
@@ -1958,6 +2007,63 @@ ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const 
     for (auto& e : ev) cudaEventDestroy(e);
     if (s != CCX_OK) return s;
     return leave(pr);
+}
+}  // namespace
+
+extern "C" {
+
+ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts, double* slice_ms,
+                               double* reduce_ms) {
+    g_err.clear();
+    if (!pr || !slice_ms || !reduce_ms) return fail(CCX_EINVAL, "NULL argument");
+    if (!std::isfinite(gamma) || gamma < 0.0) return fail(CCX_EINVAL, "gamma must be finite and >= 0");
+    if (n_iter < 1) return fail(CCX_EINVAL, "n_iter must be >= 1");
+    ccx_opts o;
+    ccx_status s = resolve_opts(pr, opts, &o);
+    if (s != CCX_OK) return s;
+    apply_opts(pr, o);
+    return time_iterations_impl(pr, gamma, n_iter, o, slice_ms, reduce_ms);
+}
+
+ccx_status ccx_tune_grid(ccx_problem* pr, int g_min, int* g_out, double* ms_out) {
+    g_err.clear();
+    if (!pr || !g_out) return fail(CCX_EINVAL, "NULL argument");
+    if (pr->path_started)
+        return fail(CCX_EINVAL, "ccx_tune_grid runs iterations from Y_0: call it before the first solve or after "
+                                "ccx_reset_path");
+    if (pr->ei.empty()) return fail(CCX_EINVAL, "no edges");
+    ccx_opts o;
+    ccx_status s = resolve_opts(pr, nullptr, &o);
+    if (s != CCX_OK) return s;
+    pr->tuned_G = 0;
+    const int gmax = grid_of_cap(pr, 0);
+    const int lo = std::max(1, std::min(g_min, gmax));
+    int best = gmax;
+    double best_cost = 0.0, best_ms = 0.0;
+    for (int G = gmax; G >= lo; G = (G == lo) ? 0 : std::max(lo, G / 2)) {
+        o.max_ctas = G;
+        apply_opts(pr, o);
+        double a = 0.0, b = 0.0;
+        pr->path_started = false;
+        s = time_iterations_impl(pr, 0.0, 3, o, &a, &b);      // warm-up: kernel attributes, caches
+        if (s == CCX_OK) s = time_iterations_impl(pr, 0.0, 16, o, &a, &b);
+        if (s != CCX_OK) {
+            pr->path_started = false;
+            return s;
+        }
+        const double ms = a + b;
+        const double cost = ms * G;                            // SM-milliseconds per iteration
+        if (G == gmax || cost < best_cost * 0.98) {
+            best = G;
+            best_cost = cost;
+            best_ms = ms;
+        }
+    }
+    pr->path_started = false;                                  // the next solve starts from Y_0
+    pr->tuned_G = best == gmax ? 0 : best;
+    *g_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return CCX_OK;
 }
 
 uint64_t ccx_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -169,6 +169,8 @@ int pd_reduce_blocks(int le);
 cudaError_t launch_pack_input(const float* X, const uint8_t* mask, int64_t n, int64_t p, int64_t ld_in,
                               float* Xf, double* Xd, uint32_t* maskbits, int ld, int ldw, int* bad_count,
                               cudaStream_t s);
+cudaError_t launch_standardize(float* Xf, double* Xd, const uint32_t* maskbits, int n, int p, int ld, int ldw,
+                               double* work, cudaStream_t s);
 cudaError_t launch_fill_missing(const float* Xf, const double* Xd, const uint32_t* maskbits, int n, int p,
                                 int ld, int ldw, double* colmean, float* Y0f, double* Y0d, double* ss,
                                 cudaStream_t s);
@@ -192,9 +194,10 @@ struct KnnResult {
 };
 // geo: NULL (Euclidean rule), or device (latitude, longitude) pairs in degrees for the
 // composite distance alpha ||y_i - y_j|| + (1 - alpha) g_ij (geodesic: great-circle g)
+// gram: 0 tensor cores on TF32 operands, 1 tensor cores on BF16 operands, 2 FP32 CUDA cores
 cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
                       cudaStream_t s, KnnResult* out, std::string* err, const double* geo = nullptr,
-                      double alpha = 1.0, int geodesic = 0);
+                      double alpha = 1.0, int geodesic = 0, int gram = 0);
 // principal axes of Y_0 (pc_kernels.cu): axes q x p doubles (device), variances on the host
 int pc_max_axes();
 cudaError_t pc_axes(const float* Y0f, const double* mean, int n, int p, int ld, int q, double* axes, double* var_h,

@@ -1,23 +1,29 @@
 // Gram matrix G = Y Y^T of the kNN weight rule (Calibration of Weights, Eq. 8:
 // d2_ij = ||y_i||^2 + ||y_j||^2 - 2 <y_i, y_j>) on the 5th-generation tensor
-// cores: tcgen05.mma kind::tf32 reading FP32 rows straight from shared memory,
-// accumulating in FP32 in tensor memory.
+// cores, accumulating in FP32 in tensor memory: tcgen05.mma kind::tf32 reading
+// FP32 rows straight from shared memory, or kind::f16 on BF16 rows (a copy of Y
+// rounded to nearest BF16 by a conversion kernel).  In both cases a stage holds
+// 128 bytes of every row, i.e. 32 TF32 or 64 BF16 values, and takes four MMAs
+// of K = 8 (TF32) or K = 16 (BF16).
 //
 // One CTA per 128 x 128 output tile of the upper triangle (the lower one is
-// written as its mirror).  Warp 0 lane 0 streams 128-row x 32-column tiles of
-// Y (128 bytes per row, 128-byte swizzle) into a 4-stage ring with TMA; warp 1
-// lane 0 issues four 128 x 128 x 8 MMAs per stage and returns each stage to the
+// written as its mirror).  Warp 0 lane 0 streams 128-row tiles of Y, 128 bytes
+// per row (128-byte swizzle), into a 4-stage ring with TMA; warp 1 lane 0
+// issues the stage's four 128 x 128 MMAs and returns each stage to the
 // producer with tcgen05.commit; all four warps then read the accumulator out of
 // tensor memory (tcgen05.ld, one 32-lane quarter per warp).  Every wait is
 // bounded: on a timeout the kernel raises an error flag, releases its tensor
 // memory and returns, and the host reports the failure.
 //
-// The products are formed from TF32-rounded inputs, so the result is an
-// approximation with a stated error bound (returned through `unit`); the kNN
-// rule uses it only to select candidates and recomputes their distances exactly.
+// The products are formed from TF32- or BF16-rounded inputs, so the result is
+// an approximation with a stated error bound (returned through `unit`); the
+// kNN rule uses it only to select candidates and recomputes their distances
+// exactly, so the edge set does not depend on which input rounding was used.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+
+#include <cuda_bf16.h>
 
 #include <cstdint>
 #include <mutex>
@@ -28,10 +34,10 @@ namespace ccx {
 namespace {
 
 constexpr int kBM = 128, kBN = 128;       // output tile
-constexpr int kBK = 32;                   // K per stage: 32 floats = 128 bytes = one swizzle row
-constexpr int kMmaK = 8;                  // K of one kind::tf32 MMA (32 bytes)
+constexpr int kRowBytes = 128;            // bytes of a row per stage: one swizzle row
+constexpr int kMmaBytes = 32;             // K bytes of one MMA (8 TF32 or 16 BF16 values)
 constexpr int kStages = 4;
-constexpr int kTileBytes = kBM * kBK * 4; // 16 KB per operand tile
+constexpr int kTileBytes = kBM * kRowBytes; // 16 KB per operand tile
 constexpr int kStageBytes = 2 * kTileBytes;
 constexpr int kThreads = 128;
 constexpr uint32_t kTmemCols = 128;       // 128 lanes x 128 FP32 columns
@@ -96,17 +102,22 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
-// K-major, N = 128, M = 128.
-constexpr uint32_t kInstrDesc = (1u << 4)                       // D format: F32
-                                | (2u << 7)                     // A format: TF32
-                                | (2u << 10)                    // B format: TF32
-                                | ((uint32_t)(kBN >> 3) << 17)  // N / 8
-                                | ((uint32_t)(kBM >> 4) << 24); // M / 16
+// Instruction descriptors: FP32 accumulator, A and B both K-major, N = 128,
+// M = 128; operand format 2 = TF32 (kind::tf32), 1 = BF16 (kind::f16).
+constexpr uint32_t instr_desc(uint32_t ab_format) {
+    return (1u << 4)                        // D format: F32
+           | (ab_format << 7)               // A format
+           | (ab_format << 10)              // B format
+           | ((uint32_t)(kBN >> 3) << 17)   // N / 8
+           | ((uint32_t)(kBM >> 4) << 24);  // M / 16
+}
 
+template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1)
-    gram_tf32_kernel(const __grid_constant__ CUtensorMap tmap, int n, int ktiles, float* __restrict__ G,
-                     int* __restrict__ err) {
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int n, int ktiles, float* __restrict__ G,
+                   int* __restrict__ err) {
+    constexpr int kBK = BF16 ? 64 : 32;    // values per row per stage (128 bytes)
+    constexpr uint32_t kInstrDesc = instr_desc(BF16 ? 1u : 2u);
     const int bm = blockIdx.y, bn = blockIdx.x;
     if (bn < bm) return;   // the lower triangle is written as the mirror of the upper one
     extern __shared__ unsigned char smem_raw[];
@@ -159,18 +170,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a = smem_u32(sm + (size_t)s * kStageBytes);
             const uint32_t b = a + kTileBytes;
 #pragma unroll
-            for (int kk = 0; kk < kBK / kMmaK; ++kk) {
-                const uint64_t da = smem_desc_sw128(a + kk * kMmaK * 4);
-                const uint64_t db = smem_desc_sw128(b + kk * kMmaK * 4);
+            for (int kk = 0; kk < kRowBytes / kMmaBytes; ++kk) {
+                const uint64_t da = smem_desc_sw128(a + kk * kMmaBytes);
+                const uint64_t db = smem_desc_sw128(b + kk * kMmaBytes);
                 const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n"
-                    ".reg .pred p;\n"
-                    "setp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
-                    "}\n" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(kInstrDesc), "r"(acc)
-                    : "memory");
+                if constexpr (BF16) {
+                    asm volatile(
+                        "{\n"
+                        ".reg .pred p;\n"
+                        "setp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                        "}\n" ::"r"(tmem),
+                        "l"(da), "l"(db), "r"(kInstrDesc), "r"(acc)
+                        : "memory");
+                } else {
+                    asm volatile(
+                        "{\n"
+                        ".reg .pred p;\n"
+                        "setp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+                        "}\n" ::"r"(tmem),
+                        "l"(da), "l"(db), "r"(kInstrDesc), "r"(acc)
+                        : "memory");
+                }
             }
             // the stage goes back to the producer once these MMAs have read it
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -221,6 +243,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// rows of Y rounded to nearest BF16 (n x ld; the padding columns stay 0)
+__global__ void to_bf16_kernel(const float* __restrict__ Y, size_t total, __nv_bfloat16* __restrict__ Yb) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
+        Yb[k] = __float2bfloat16_rn(Y[k]);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -239,51 +267,84 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-cudaError_t launch_gram_tc(const float* Y, int n, int p, int ld, float* G, double* unit, cudaStream_t s) {
+cudaError_t launch_gram_tc(const float* Y, int n, int p, int ld, float* G, double* unit, cudaStream_t s, int bf16) {
     int dev = 0, major = 0, minor = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     if (e != cudaSuccess) return e;
-    if (major != 10 || n < 1 || ld % kBK != 0 || (reinterpret_cast<uintptr_t>(Y) & 15u) != 0)
+    if (major != 10 || n < 1 || ld % 32 != 0 || (reinterpret_cast<uintptr_t>(Y) & 15u) != 0)
         return cudaErrorNotSupported;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
+    const int kbk = bf16 ? 64 : 32;                      // values per 128-byte stage row
+    const size_t esz = bf16 ? 2 : 4;
+    __nv_bfloat16* Yb = nullptr;
+    const void* base = Y;
+    if (bf16) {
+        if ((e = cudaMallocAsync(&Yb, sizeof(__nv_bfloat16) * (size_t)n * ld, s)) != cudaSuccess) return e;
+        const size_t total = (size_t)n * ld;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 8192) blocks = 8192;
+        count_launches(1);
+        to_bf16_kernel<<<blocks, 256, 0, s>>>(Y, total, Yb);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            cudaFreeAsync(Yb, s);
+            return e;
+        }
+        base = Yb;
+    }
     // Y as a 2-D tensor: inner dimension ld columns (the padding columns are 0),
-    // outer n rows; boxes of 32 columns (128 bytes) x 128 rows, rows past n read as 0
+    // outer n rows; boxes of 128 bytes x 128 rows, entries past n (or past ld in
+    // the last BF16 stage) read as 0
     CUtensorMap map;
     const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * esz};
+    const cuuint32_t box[2] = {(cuuint32_t)kbk, (cuuint32_t)kBM};
     const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(Y), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    if (enc(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+            const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        if (Yb) cudaFreeAsync(Yb, s);
         return cudaErrorNotSupported;
-    static int attr_set = 0;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(gram_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr_set = 1;
+    }
+    auto kern = bf16 ? gram_tc_kernel<true> : gram_tc_kernel<false>;
+    static int attr_set[2] = {0, 0};
+    if (!attr_set[bf16 ? 1 : 0]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) {
+            if (Yb) cudaFreeAsync(Yb, s);
+            return e;
+        }
+        attr_set[bf16 ? 1 : 0] = 1;
     }
     int* err = nullptr;
-    if ((e = cudaMallocAsync(&err, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync(&err, sizeof(int), s)) != cudaSuccess) {
+        if (Yb) cudaFreeAsync(Yb, s);
+        return e;
+    }
     if ((e = cudaMemsetAsync(err, 0, sizeof(int), s)) != cudaSuccess) return e;
     const int nt = (n + kBM - 1) / kBM;
+    const int ktiles = (ld + kbk - 1) / kbk;
     count_launches(1);
-    gram_tf32_kernel<<<dim3(nt, nt), kThreads, kSmemBytes, s>>>(map, n, ld / kBK, G, err);
+    kern<<<dim3(nt, nt), kThreads, kSmemBytes, s>>>(map, n, ktiles, G, err);
     e = cudaGetLastError();
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(err, s);
+    if (Yb) cudaFreeAsync(Yb, s);
     if (e != cudaSuccess) return e;
     if (herr) return cudaErrorLaunchTimeout;   // a bounded wait gave up: no result
-    // |G_ij - <y_i, y_j>| <= unit ||y_i|| ||y_j||: TF32 operands (relative rounding
-    // below 2^-10 each, so 2^-9 + 2^-20 per product, Cauchy-Schwarz over the row),
-    // the float rounding of the filled rows (2 * 2^-24) and FP32 accumulation over
-    // ld terms, allowed 4 units of 2^-24 per addition
-    *unit = 1.0 / 512.0 + 1.0 / 1048576.0 + 2.0 / 16777216.0 + (double)(ld + 64) * 4.0 / 16777216.0;
+    // |G_ij - <y_i, y_j>| <= unit ||y_i|| ||y_j||: the rounded operands (TF32:
+    // the low mantissa bits dropped, relative error below 2^-10 each, so 2^-9 +
+    // 2^-20 per product; BF16: rounded to nearest, below 2^-8 each, so 2^-7 +
+    // 2^-16 per product), Cauchy-Schwarz over the row, the float rounding of
+    // the filled rows (2 * 2^-24) and FP32 accumulation over ld terms, allowed
+    // 4 units of 2^-24 per addition
+    const double prod = bf16 ? 1.0 / 128.0 + 1.0 / 65536.0 : 1.0 / 512.0 + 1.0 / 1048576.0;
+    *unit = prod + 2.0 / 16777216.0 + (double)(ld + 64) * 4.0 / 16777216.0;
     (void)p;
     return cudaSuccess;
 }

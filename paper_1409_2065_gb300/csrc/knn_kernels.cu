@@ -30,7 +30,7 @@ namespace ccx {
 // defined in gram_tc.cu: G = Y Y^T on the tensor cores; returns cudaErrorNotSupported
 // when the shape is outside the kernel's tiling, and the per-entry relative
 // input rounding it used through *unit.
-cudaError_t launch_gram_tc(const float* Y, int n, int p, int ld, float* G, double* unit, cudaStream_t s);
+cudaError_t launch_gram_tc(const float* Y, int n, int p, int ld, float* G, double* unit, cudaStream_t s, int bf16);
 
 namespace {
 
@@ -279,7 +279,8 @@ void knn_set_exact_rows(const float* Xf, const uint32_t* bits, const double* col
 // exact squared distances nd2, each row ascending by (d2, j).  The caller frees
 // *nbr and *nd2.
 static cudaError_t knn_lists(const float* Y0f, int n, int p, int ld, int kk, cudaStream_t s, int** nbr_out,
-                             double** nd2_out, const double* geo = nullptr, double alpha = 1.0, int geodesic = 0) {
+                             double** nd2_out, const double* geo = nullptr, double alpha = 1.0, int geodesic = 0,
+                             int gram = 0) {
     const KnnDeviceArgs ka = g_knn_args;
     const int use_all = (kk >= n - 1) ? 1 : 0;
     cudaError_t e;
@@ -302,7 +303,7 @@ static cudaError_t knn_lists(const float* Y0f, int n, int p, int ld, int kk, cud
     if ((e = cudaGetLastError()) != cudaSuccess) return cleanup(), e;
     if (!use_all) {
         if ((e = cudaMalloc(&G, sizeof(float) * (size_t)n * n)) != cudaSuccess) return cleanup(), e;
-        e = launch_gram_tc(Y0f, n, p, ld, G, &gunit, s);
+        e = gram == 2 ? cudaErrorNotSupported : launch_gram_tc(Y0f, n, p, ld, G, &gunit, s, gram == 1 ? 1 : 0);
         if (e == cudaErrorNotSupported) {
             (void)cudaGetLastError();
             dim3 grid((n + 63) / 64, (n + 63) / 64);
@@ -416,7 +417,7 @@ cudaError_t knn_min_connected_k(const float* Y0f, int n, int p, int ld, int k_ma
 
 cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
                       cudaStream_t s, KnnResult* out, std::string* err, const double* geo, double alpha,
-                      int geodesic) {
+                      int geodesic, int gram) {
     if (n > 4096) {
         *err = "kNN build supports n <= 4096 in this build";
         return cudaErrorNotSupported;
@@ -429,7 +430,7 @@ cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi,
     if (kk <= 0) return cudaSuccess;
     int* nbr = nullptr;
     double* nd2 = nullptr;
-    cudaError_t e = knn_lists(Y0f, n, p, ld, kk, s, &nbr, &nd2, geo, alpha, geodesic);
+    cudaError_t e = knn_lists(Y0f, n, p, ld, kk, s, &nbr, &nd2, geo, alpha, geodesic, gram);
     if (e != cudaSuccess) return e;
     auto cleanup = [&]() {
         cudaFree(nbr);

@@ -5,6 +5,11 @@
 // missing entries to 0, bit-packs the mask (padding marked observed) and
 // counts non-finite observed entries and rows without any observed entry.
 //
+// standardize: each column centred on the mean of its observed entries and
+// divided by their standard deviation (divisor = their count; centred only when
+// that deviation is 0), in double and rounded once (Methods: the predictors are
+// standardised).
+//
 // fill_missing: Y_0 = X with each missing entry replaced by its column's
 // observed mean (Methods, "Missing Data", start of the iteration; also the
 // fill used for the weights), and ||Y_c||_F^2, the squared Frobenius norm of
@@ -99,6 +104,45 @@ __global__ void fill_kernel(const float* __restrict__ Xf, const uint32_t* __rest
     }
 }
 
+// observed mean and standard deviation of each column (two passes in double)
+__global__ void column_stats_kernel(const float* __restrict__ Xf, const uint32_t* __restrict__ bits, int n, int p,
+                                    int ld, int ldw, double* __restrict__ mean, double* __restrict__ scale) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p) return;
+    double s = 0.0;
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        if (bits && !((bits[(size_t)i * ldw + (c >> 5)] >> (c & 31)) & 1u)) continue;
+        s += (double)Xf[(size_t)i * ld + c];
+        ++cnt;
+    }
+    const double mu = cnt > 0 ? s / cnt : 0.0;
+    double v = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (bits && !((bits[(size_t)i * ldw + (c >> 5)] >> (c & 31)) & 1u)) continue;
+        const double d = (double)Xf[(size_t)i * ld + c] - mu;
+        v += d * d;
+    }
+    const double sd = cnt > 0 ? sqrt(v / cnt) : 0.0;
+    mean[c] = mu;
+    scale[c] = sd > 0.0 ? sd : 1.0;
+}
+
+// observed entries -> (x - mean) / scale; missing entries and padding stay 0
+__global__ void standardize_kernel(float* __restrict__ Xf, double* __restrict__ Xd, const uint32_t* __restrict__ bits,
+                                   int n, int p, int ld, int ldw, const double* __restrict__ mean,
+                                   const double* __restrict__ scale) {
+    const size_t total = (size_t)n * ld;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k / ld), c = (int)(k % ld);
+        if (c >= p) continue;
+        if (bits && !((bits[(size_t)i * ldw + (c >> 5)] >> (c & 31)) & 1u)) continue;
+        const double z = ((double)Xf[k] - mean[c]) / scale[c];
+        Xf[k] = (float)z;
+        if (Xd) Xd[k] = z;
+    }
+}
+
 // per-column sum of squared deviations of Y_0 (double), then one fixed-order total
 __global__ void centred_ss_kernel(const float* __restrict__ Y0f, const double* __restrict__ Y0d, int n, int p, int ld,
                                   const double* __restrict__ colmean, double* __restrict__ colss) {
@@ -141,6 +185,20 @@ cudaError_t launch_pack_input(const float* X, const uint8_t* mask, int64_t n, in
     if (e != cudaSuccess || !mask) return e;
     count_launches(1);
     pack_mask_kernel<<<(unsigned)n, 128, 0, s>>>(mask, n, p, ld_in, maskbits, ldw, bad_count + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_standardize(float* Xf, double* Xd, const uint32_t* maskbits, int n, int p, int ld, int ldw,
+                               double* work, cudaStream_t s) {
+    // work holds 2 * ld doubles: the column means, then the scales
+    const int tb = 128;
+    count_launches(1);
+    column_stats_kernel<<<(p + tb - 1) / tb, tb, 0, s>>>(Xf, maskbits, n, p, ld, ldw, work, work + ld);
+    size_t total = (size_t)n * ld;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    count_launches(1);
+    standardize_kernel<<<blocks, 256, 0, s>>>(Xf, Xd, maskbits, n, p, ld, ldw, work, work + ld);
     return cudaGetLastError();
 }
 

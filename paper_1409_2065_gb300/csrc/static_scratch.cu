@@ -3,7 +3,9 @@
 //
 // The buffer is one file-scope array shared by every call on a device: a call
 // overwrites entries [0, m) before it reads them, so nothing has to start at
-// zero, and two calls whose kernels overlap on the GPU race on it.
+// zero, and two calls whose kernels overlap on the GPU race on it.  Its device
+// address is looked up once per device and kept; it belongs to the context that
+// was current then, so it is not valid after a device reset in the process.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -10,7 +10,7 @@ boundary):
 * ``gaussian_mixture`` -- ``n`` points in ``p`` dimensions split into
   ``k`` equal clusters; cluster means ~ N(0, 9 I), points = mean + N(0, I).
   This is the "plain" workload (n=200, p=10, 4 clusters, seed 0).
-* ``genotype_like`` -- Balding-Nichols allele frequencies: ancestral
+* ``genotype_codes`` / ``genotype_like`` -- Balding-Nichols allele frequencies: ancestral
   frequency p0 ~ U(0.05, 0.5) per SNP, population frequency
   ~ Beta(p0 (1-F)/F, (1-p0)(1-F)/F), genotype ~ Binomial(2, freq); codes
   are standardised with the observed entries and a fraction of entries is
@@ -34,6 +34,7 @@ import numpy as np
 
 __all__ = [
     "gaussian_mixture",
+    "genotype_codes",
     "genotype_like",
     "expression_like",
     "batched_problems",
@@ -78,11 +79,11 @@ def gaussian_mixture(n: int = 200, p: int = 10, k: int = 4, seed: int = 0,
     return X.astype(np.float32), lab
 
 
-def genotype_like(n: int = 1000, p: int = 10000, pops: int = 5, seed: int = 1,
-                  fst: float = 0.05, frac_missing: float = 0.05):
-    """Balding-Nichols genotypes, standardised on observed entries.
+def genotype_codes(n: int = 1000, p: int = 10000, pops: int = 5, seed: int = 1,
+                   fst: float = 0.05, frac_missing: float = 0.05):
+    """Balding-Nichols genotype codes {0, 1, 2}, unstandardised.
 
-    Returns (X float32 n x p, mask uint8 n x p (1 = observed), population ids).
+    Returns (codes float32 n x p, mask uint8 n x p (1 = observed), population ids).
     """
     rng = np.random.default_rng(seed)
     p0 = rng.uniform(0.05, 0.5, size=p)
@@ -91,8 +92,18 @@ def genotype_like(n: int = 1000, p: int = 10000, pops: int = 5, seed: int = 1,
     freq = rng.beta(a, b, size=(pops, p))
     sizes = [n // pops + (1 if c < n % pops else 0) for c in range(pops)]
     lab = np.repeat(np.arange(pops), sizes)
-    G = rng.binomial(2, freq[lab]).astype(np.float64)
+    G = rng.binomial(2, freq[lab]).astype(np.float32)
     mask = random_mask(rng, n, p, frac_missing)
+    return G, mask, lab
+
+
+def genotype_like(n: int = 1000, p: int = 10000, pops: int = 5, seed: int = 1,
+                  fst: float = 0.05, frac_missing: float = 0.05):
+    """Balding-Nichols genotypes (genotype_codes), standardised on observed entries.
+
+    Returns (X float32 n x p, mask uint8 n x p (1 = observed), population ids).
+    """
+    G, mask, lab = genotype_codes(n, p, pops, seed, fst, frac_missing)
     X = standardize_observed(G, mask)
     return X.astype(np.float32), mask, lab
 

@@ -20,11 +20,12 @@ five gammas from before the first fusion to complete fusion.  Stores the
 whole of U per gamma (float32), the fused flags, labels, d and each edge's
 margin |mu w d / (rho ||b||) - 1| at the oracle's fixed point.
 
-allpairs_n60_p5000.npz -- expression-like data (log-normal, 3 groups with
-150 up-shifted genes each, seed 62) with n = 60 samples and p = 5000 genes,
-all 1770 pairs weighted (phi automatic, normalised): 1250 slices, eight or
-nine per CTA.  Four gammas.  Stores 16 fixed rows of U per gamma (float32)
-and the norm of every row, the fused flags, labels, d and margins.
+allpairs_n32_p5000.npz -- expression-like data (log-normal, 3 groups with
+150 up-shifted genes each, seed 62) with n = 32 samples and p = 5000 genes,
+all 496 pairs weighted (phi automatic, normalised): 1250 slices, eight or
+nine per CTA.  Five gammas around the abrupt fusion of the complete graph.
+Stores 12 fixed rows of U per gamma (float32) and the norm of every row, the
+fused flags, labels, d and margins.
 
 threshold_edge.npz -- a 12-case problem (3 Gaussian clusters, p = 3, kNN
 k = 3, phi = 0.1) at the penalty where its first edge fuses, found by
@@ -94,18 +95,18 @@ def genotype_n48():
           "of", G.m, "converged", [r.converged for r in res])
 
 
-def allpairs_n60():
-    X, _ = synth.expression_like(60, 5000, 3, 150, seed=62)
+def allpairs_n32():
+    X, _ = synth.expression_like(32, 5000, 3, 150, seed=62)
     Xd = X.astype(np.float64)
-    ei, ej, w, _, phi = O.knn_gaussian_weights(Xd, None, 59, "auto", True)
-    G = O.EdgeGraph(60, ei, ej, w)
+    ei, ej, w, _, phi = O.knn_gaussian_weights(Xd, None, 31, "auto", True)
+    G = O.EdgeGraph(32, ei, ej, w)
     g0 = O.fusion_scale(Xd, None, ei, ej, w)
-    gammas = g0 * np.array([0.05, 0.2, 0.5, 2.0])
+    gammas = g0 * np.array([0.03, 0.062, 0.065, 0.068, 0.12])
     res = O.solve_path(Xd, None, G, gammas, tol=1e-12)
-    rows = np.sort(np.random.default_rng(63).choice(60, 16, replace=False))
-    np.savez_compressed(os.path.join(HERE, "allpairs_n60_p5000.npz"), ei=ei, ej=ej, w=w, gammas=gammas, g0=g0,
+    rows = np.sort(np.random.default_rng(63).choice(32, 12, replace=False))
+    np.savez_compressed(os.path.join(HERE, "allpairs_n32_p5000.npz"), ei=ei, ej=ej, w=w, gammas=gammas, g0=g0,
                         **_path_arrays(res, G, rows))
-    print("allpairs_n60_p5000: iters", [r.iters for r in res], "fused", [int(r.fused.sum()) for r in res],
+    print("allpairs_n32_p5000: iters", [r.iters for r in res], "fused", [int(r.fused.sum()) for r in res],
           "of", G.m, "converged", [r.converged for r in res])
 
 
@@ -155,7 +156,7 @@ def threshold_edge():
           "fused", int(r.fused.sum()))
 
 
-CASES = {"plain": plain_n200, "genotype": genotype_n48, "allpairs": allpairs_n60, "threshold": threshold_edge}
+CASES = {"plain": plain_n200, "genotype": genotype_n48, "allpairs": allpairs_n32, "threshold": threshold_edge}
 
 if __name__ == "__main__":
     for name in (sys.argv[1:] or list(CASES)):

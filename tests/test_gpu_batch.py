@@ -109,3 +109,39 @@ def test_batch_reports_errors_per_problem(ccx):
         assert np.array_equal(Us[i], ref[i])
     for pr in probs + [bad]:
         pr.close()
+
+
+def test_tuned_grids_batch_equals_alone(ccx):
+    """ccx_tune_grid picks a grid per problem (from timing); a batch of tuned problems gives, for each,
+    exactly the result of solving it alone with the same grid, and agrees with the default grid within
+    the FP32 parity bar (1e-4 relative, the grid changes only the rounding of partial sums)."""
+    specs = _problem_set(6, 17)
+    probs, grids, tuned = [], [], []
+    for sp in specs:
+        pr = _build(ccx, sp, 0)
+        g, ms = pr.tune_grid(1)
+        assert g >= 1 and ms > 0.0
+        tuned.append(g)
+        probs.append(pr)
+        grids.append(_grid(pr, sp[3]))
+    Us, Ls, stats, status, st = ccx.solve_batch(probs, grids, max_active=6)
+    assert st == 0 and all(s == 0 for s in status), status
+    for i, sp in enumerate(specs):
+        alone = _build(ccx, sp, 0)
+        o = ccx.opts_default()
+        o.max_ctas = tuned[i]
+        U, L, _, s1 = alone.solve_path(grids[i], o)
+        assert s1 == 0
+        assert np.array_equal(Us[i], U) and np.array_equal(Ls[i], L), i
+        alone.reset_path()
+        U0, L0, _, s0 = alone.solve_path(grids[i])
+        assert s0 == 0
+        for g in range(len(grids[i])):
+            assert np.linalg.norm(U0[g] - U[g]) <= 1e-4 * np.linalg.norm(U0[g]), (i, g)
+        alone.close()
+    for pr in probs:
+        pr.close()
+    with pytest.raises(ccx.CcxError):          # tuning needs a fresh path
+        pr2 = _build(ccx, specs[0], 0)
+        pr2.solve_path([0.1])
+        pr2.tune_grid(1)

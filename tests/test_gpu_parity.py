@@ -140,15 +140,17 @@ def test_knn_matches_oracle_missing_normalized(ccx):
     assert abs(w.sum() - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("gram", [0, 1, 2])
 @pytest.mark.parametrize("n,p,k,frac", [(400, 2000, 10, 0.05), (130, 37, 5, 0.0), (257, 300, 9, 0.1)])
-def test_knn_tensor_core_gram_shapes(ccx, n, p, k, frac):
-    """Candidate selection from the tensor-core Gram: tiles with ragged rows (n not a multiple of 128),
-    short and long K, missing data; the edge set must equal brute force exactly."""
+def test_knn_tensor_core_gram_shapes(ccx, n, p, k, frac, gram):
+    """Candidate selection from the Gram (tensor cores on TF32 or BF16 operands, or FP32 CUDA cores):
+    tiles with ragged rows (n not a multiple of 128), short and long K (p = 300 leaves half a BF16
+    stage), missing data; the edge set must equal brute force exactly for every Gram."""
     X, mask, _ = synth.genotype_like(n, p, 5, seed=31, fst=0.05, frac_missing=frac)
     if frac == 0.0:
         mask = None
     pr = ccx.Problem(X, mask, ccx.CCX_FP32)
-    pr.build_knn(k, phi_auto=True, normalize=True)
+    pr.build_knn(k, phi_auto=True, normalize=True, gram=gram)
     ei, ej, w = pr.get_edges()
     oei, oej, ow, _, _ = O.knn_gaussian_weights(X.astype(np.float64), mask, k, "auto", True)
     assert np.array_equal(ei, oei) and np.array_equal(ej, oej)
@@ -376,3 +378,39 @@ def test_invalid_inputs(ccx):
     with pytest.raises(ccx.CcxError) as e:
         pr.solve_path([np.nan])
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_standardize_matches_oracle(ccx, precision):
+    """Observed-entry standardisation on the GPU (a constant column, a column with nothing observed,
+    5 % missing) equals the oracle's, rounded once to float32; the kNN weights and the path on the
+    standardised data then match the oracle's on its own standardised data."""
+    G, mask, _ = synth.genotype_codes(90, 57, 3, seed=71, fst=0.05, frac_missing=0.05)
+    G[:, 5] = 1.0                          # constant on its observed entries: centred only
+    mask[:, 9] = 0                         # nothing observed: stays 0
+    pr = ccx.Problem(G, mask, precision, standardize=True)
+    Z = O.standardize(G, mask)
+    Y = pr.get_start()
+    ref = O.fill_missing(Z.astype(np.float32).astype(np.float64), mask)
+    assert np.max(np.abs(Y - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-6
+    assert np.all(Y[:, 5] == 0.0) and np.all(Y[:, 9] == 0.0)
+    Z32 = Z.astype(np.float32)
+    pr.build_knn(6, phi_auto=True, normalize=True)
+    ei, ej, w = pr.get_edges()
+    oei, oej, ow, _, _ = O.knn_gaussian_weights(Z32.astype(np.float64), mask, 6, "auto", True)
+    assert np.array_equal(ei, oei) and np.array_equal(ej, oej)
+    assert np.allclose(w, ow, rtol=1e-6, atol=0)
+    Gr = O.EdgeGraph(90, oei, oej, ow)
+    g0 = O.fusion_scale(Z32, mask, oei, oej, ow)
+    gammas = [0.05 * g0, 0.3 * g0, 2.0 * g0]
+    U, labels, fused, stats, st = solve_fused(pr, gammas)
+    assert st == 0
+    ref_path = O.solve_path(Z32.astype(np.float64), mask, Gr, gammas, tol=1e-12)
+    compare_path(U, labels, fused, stats, ref_path, Z32, mask, Gr, 1e-4, "standardised")
+    # calling it again on standardised data changes nothing beyond rounding, and clears the edges
+    pr.get_edges()
+    import paper_1409_2065_gb300 as m
+    m.binding.standardize(pr.h)
+    assert pr.get_edges()[0].size == 0
+    assert np.max(np.abs(pr.get_start() - Y)) <= 1e-6
+    pr.close()

@@ -505,6 +505,30 @@ def test_fusion_scale_is_the_two_point_threshold():
     assert g == pytest.approx(sorted([1 / 2, 2 / 1, 4 / 4])[1])
 
 
+def test_standardize_hand_example():
+    """Observed-entry standardisation worked by hand.  Column 0 has observed 1, 3, 8: mean 4, squared
+    deviations 9, 1, 16, variance 26/3 (divisor 3), so the entries are -3, -1, 4 over sqrt(26/3).
+    Column 1 has observed 2 and 6 (the 100 at row 1 is masked): mean 4, variance 4, giving -1 and +1,
+    the missing entry 0.  Column 2 is constant on its observed entries:
+    centred only, all 0.  Column 3 has no observed entry: 0."""
+    X = np.array([[1.0, 2.0, 7.0, 1.0], [3.0, 100.0, 7.0, 2.0], [8.0, 6.0, 7.0, 3.0]])
+    mask = np.array([[1, 1, 1, 0], [1, 0, 1, 0], [1, 1, 0, 0]], np.uint8)
+    Z = O.standardize(X, mask)
+    s = np.sqrt(26.0 / 3.0)
+    assert np.allclose(Z[:, 0], [-3.0 / s, -1.0 / s, 4.0 / s], rtol=1e-15, atol=0)
+    assert Z[:, 1].tolist() == [-1.0, 0.0, 1.0]
+    assert Z[:, 2].tolist() == [0.0, 0.0, 0.0] and Z[:, 3].tolist() == [0.0, 0.0, 0.0]
+    # without a mask: every column has mean 0 and (population) variance 1 unless constant
+    rng = np.random.default_rng(4)
+    Y = rng.normal(3.0, 2.0, (9, 5))
+    Y[:, 2] = -1.5
+    Zy = O.standardize(Y, None)
+    assert np.allclose(Zy.mean(axis=0), 0.0, atol=1e-15)
+    assert np.allclose((Zy ** 2).mean(axis=0), [1, 1, 0, 1, 1], rtol=1e-14, atol=1e-30)
+    # invariant to a positive affine change of each column
+    assert np.allclose(O.standardize(4.0 * Y - 7.0, None), Zy, atol=1e-13)
+
+
 def test_fill_missing_hand_example():
     X = np.array([[1.0, 9.0], [3.0, 2.0], [8.0, 4.0]])
     mask = np.array([[1, 0], [1, 1], [0, 1]], np.uint8)
