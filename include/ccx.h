@@ -432,7 +432,8 @@ ccx_status ccx_shard_end_gamma(ccx_problem* pr, float* U_out, int32_t* labels_ou
  * Times 16 MM iterations of this problem at grids of G, G/2, G/4, ... CTAs
  * (G = one per SM, at most one per 4-column slice), down to g_min, and keeps
  * the grid with the least SM time per iteration (grid x iteration time; a
- * smaller grid is taken only when it saves at least 2 %).  Later solves of the
+ * smaller grid is taken only when it saves at least 30 %, so work-bound problems
+ * keep the whole GPU and only latency-bound ones shrink).  Later solves of the
  * problem whose options leave max_ctas at 0 use that grid, so a small problem
  * leaves SMs to the others in ccx_solve_batch or a server; results agree with
  * the default grid within the rounding of the per-CTA partial sums.  Needs the

@@ -628,9 +628,17 @@ void apply_opts(ccx_problem* pr, const ccx_opts& o) {
 
 ccx_status ensure_path(ccx_problem* pr) {
     if (pr->path_ready) {
-        // a changed grid cap resizes the per-CTA partial buffers (the path state is kept)
+        // a changed grid cap resizes the per-CTA partial buffers (the path state is kept);
+        // a captured iteration graph holds the old buffers' addresses, so it goes too
         const int G = grid_of(pr);
         if (G != pr->G) {
+            if (pr->graph) {
+                CUDA_TRY(cudaStreamSynchronize(pr->work));
+                cudaGraphExecDestroy(pr->graph);
+                pr->graph = nullptr;
+                pr->graph_chunk = 0;
+            }
+            CUDA_TRY(cudaStreamSynchronize(pr->work));
             cudaFree(pr->Pnb);
             cudaFree(pr->Ps);
             pr->Pnb = nullptr;
@@ -2053,7 +2061,10 @@ ccx_status ccx_tune_grid(ccx_problem* pr, int g_min, int* g_out, double* ms_out)
         }
         const double ms = a + b;
         const double cost = ms * G;                            // SM-milliseconds per iteration
-        if (G == gmax || cost < best_cost * 0.98) {
+        // a smaller grid must save a good part of the SM time: when the cost is only
+        // level (a work-bound problem), a small grid leaves a batch a long tail in
+        // which the last problems run on few SMs
+        if (G == gmax || cost < best_cost * 0.7) {
             best = G;
             best_cost = cost;
             best_ms = ms;

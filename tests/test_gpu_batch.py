@@ -145,3 +145,30 @@ def test_tuned_grids_batch_equals_alone(ccx):
         pr2 = _build(ccx, specs[0], 0)
         pr2.solve_path([0.1])
         pr2.tune_grid(1)
+
+
+def test_grid_changes_between_solves_rebuild_the_iteration_graph(ccx):
+    """A solve on a smaller grid reallocates the per-CTA partial buffers; the next solve on the first
+    grid must not reuse the iteration graph captured before (it holds the old buffers).  Same problem,
+    default grid -> 8 CTAs -> default grid (and tuning in between): the last result equals the first."""
+    sp = _problem_set(1, 23)[0]
+    pr = _build(ccx, sp, 0)
+    gam = _grid(pr, 3)
+    U1, L1, _, s1 = pr.solve_path(gam)
+    o = ccx.opts_default()
+    o.max_ctas = 8
+    pr.reset_path()
+    U2, _, _, s2 = pr.solve_path(gam, o)
+    pr.reset_path()
+    U3, L3, _, s3 = pr.solve_path(gam)
+    assert s1 == s2 == s3 == 0
+    assert np.array_equal(U1, U3) and np.array_equal(L1, L3)
+    pr.reset_path()
+    g, _ = pr.tune_grid(1)
+    U4, L4, _, s4 = pr.solve_path(gam)
+    fresh = _build(ccx, sp, 0)
+    o.max_ctas = g
+    U5, L5, _, s5 = fresh.solve_path(gam, o)
+    assert s4 == s5 == 0 and np.array_equal(U4, U5) and np.array_equal(L4, L5)
+    pr.close()
+    fresh.close()
