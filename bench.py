@@ -423,6 +423,9 @@ def main():
     ap.add_argument("--gram-compare", action="store_true",
                     help="instead of the default step: time the kNN weights of the workload with the Gram on "
                          "TF32 and BF16 tensor cores and on FP32 CUDA cores, and check the edge sets agree")
+    ap.add_argument("--slice-variant", type=int, default=0, choices=[0, 1, 2],
+                    help="staging of the iteration kernel's slices: 0 automatic, 1 double buffer where it fits, "
+                         "2 single buffer")
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -444,6 +447,8 @@ def main():
         run_serve(args, ccx, torch, rank)
         return
     W = workload(args.workload)
+    opts = ccx.opts_default()
+    opts.slice_variant = args.slice_variant
     n, p = W["X"].shape
     Xd = torch.from_numpy(W["X"]).cuda()
     Md = torch.from_numpy(W["mask"]).cuda() if W["mask"] is not None else None
@@ -547,9 +552,9 @@ def main():
                           "oracle_cores": os.cpu_count()}), flush=True)
         return
     if args.iterations_only:
-        slice_ms, reduce_ms = pr.time_iterations(float(gammas[len(gammas) // 2]), args.iterations_only)
-        print(json.dumps({"workload": W["desc"], "iterations": args.iterations_only, "slice_ms": slice_ms,
-                          "reduce_ms": reduce_ms}), flush=True)
+        slice_ms, reduce_ms = pr.time_iterations(float(gammas[len(gammas) // 2]), args.iterations_only, opts)
+        print(json.dumps({"workload": W["desc"], "iterations": args.iterations_only, "slice_variant": args.slice_variant,
+                          "slice_ms": slice_ms, "reduce_ms": reduce_ms}), flush=True)
         return
     U_dev = torch.empty((G, n, p), dtype=torch.float32, device="cuda")
     L_dev = torch.empty((G, n), dtype=torch.int32, device="cuda")
@@ -558,7 +563,7 @@ def main():
     def step():
         pr.build_knn(W["k"], phi=W.get("phi", 0.0), phi_auto=W.get("phi_auto", False), normalize=W["normalize"])
         pr.reset_path()
-        _, _, stats, _ = pr.solve_path(gammas, device=True, U_out=U_dev, labels_out=L_dev)
+        _, _, stats, _ = pr.solve_path(gammas, opts, device=True, U_out=U_dev, labels_out=L_dev)
         return stats
 
     for _ in range(args.warmup):
@@ -596,7 +601,7 @@ def main():
 
     # roofline of the fused node/edge kernel, timed on its own stream
     mid = float(gammas[len(gammas) // 2])
-    slice_ms, reduce_ms = pr.time_iterations(mid, 200)
+    slice_ms, reduce_ms = pr.time_iterations(mid, 200, opts)
     frac_missing = 0.0 if W["mask"] is None else float(1.0 - W["mask"].mean())
     p4 = (p + 3) // 4 * 4
     # algorithmic bytes of one MM iteration by the method's own accounting
@@ -624,7 +629,7 @@ def main():
         def e2e_step():
             q = ccx.Problem(W["X"], W["mask"], ccx.CCX_FP32)
             q.build_knn(W["k"], phi=W.get("phi", 0.0), phi_auto=W.get("phi_auto", False), normalize=W["normalize"])
-            _, _, st2, _ = q.solve_path(gammas, U_out=Uh, labels_out=Lh)
+            _, _, st2, _ = q.solve_path(gammas, opts, U_out=Uh, labels_out=Lh)
             q.close()
             return st2
         # the device arm's warm-up steps already loaded the kernels; each call
