@@ -588,6 +588,14 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     const double gamma = st->gamma, rho = st->rho;
     double lhs = 0.0;
     bool near = false;
+    // this edge's previous t and its node-sweep positions, requested with its weight
+    // so that one round trip to L2 serves them all
+    R told = (R)0;
+    int2 qp = make_int2(0, 0);
+    if (grp == 0 && e >= 0) {
+        told = P.t[st->par][2 * (size_t)LA + 2 * (size_t)pos];
+        qp = P.posA[pos];
+    }
     if (grp == 0) {
         double nb = 0.0;
         if (e >= 0) {
@@ -634,7 +642,6 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
         }
     }
     if (grp == 0) {
-        const R* tEin = P.t[st->par] + 2 * (size_t)LA;
         R* tAout = P.t[st->par ^ 1];          // (t_{m+1}, t_m) replaces (t_m, t_{m-1})
         R* tEout = tAout + 2 * (size_t)LA;
         bool fz = false;
@@ -644,11 +651,9 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
             const double rhs = rho * nb;
             fz = lhs >= rhs;                 // the prox returns exactly zero
             const R tnew = fz ? (R)1 : (R)(lhs / rhs);
-            const R told = tEin[2 * pos];
             tEout[2 * pos] = tnew;
             tEout[2 * pos + 1] = told;
-            const int2 qp = P.posA[pos];       // the edge's two node-sweep positions
-            tAout[2 * qp.x] = tnew;
+            tAout[2 * qp.x] = tnew;                // qp: the edge's two node-sweep positions
             tAout[2 * qp.x + 1] = told;
             tAout[2 * qp.y] = tnew;
             tAout[2 * qp.y + 1] = told;
@@ -696,17 +701,29 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
             q_dl += ps[kPsDelta];
         }
     }
-    const double rs = block_sum(q_rs, red);
-    const double stp = block_sum(q_st, red);
-    const double na = block_sum(q_na, red);
-    const double nzs = block_sum(q_nz, red);
-    const double dls = block_sum(q_dl, red);
-    const unsigned long long nf = (unsigned long long)block_sum((double)nf_l, red);
-    const unsigned long long nrec = (unsigned long long)block_sum((double)nr_l, red);
+    // seven block sums in one pass, each in the order of block_sum: a shuffle
+    // tree per warp, then the warps in order
+    constexpr int kNv = 7;
+    double v[kNv] = {q_rs, q_st, q_na, q_nz, q_dl, (double)nf_l, (double)nr_l};
+    __shared__ double redv[kReduceThreads / 32][kNv];
     __shared__ unsigned long long hsh[kReduceThreads];
+#pragma unroll
+    for (int k = 0; k < kNv; ++k) v[k] = warp_sum(v[k]);
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < kNv; ++k) redv[tid >> 5][k] = v[k];
     hsh[tid] = hash_l;
     __syncthreads();
     if (tid != 0) return;
+    double tv[kNv];
+#pragma unroll
+    for (int k = 0; k < kNv; ++k) {
+        tv[k] = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) tv[k] += redv[w][k];
+    }
+    const double rs = tv[0], stp = tv[1], na = tv[2], nzs = tv[3], dls = tv[4];
+    const unsigned long long nf = (unsigned long long)tv[5];
+    const unsigned long long nrec = (unsigned long long)tv[6];
     unsigned long long hash = 0ULL;
     for (int k = 0; k < (int)blockDim.x; ++k) hash += hsh[k];
     const double unit = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
