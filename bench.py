@@ -55,7 +55,8 @@ def workload(name: str):
     if name == "plain":
         X, _ = synth.gaussian_mixture(200, 10, 4, seed=0)
         return dict(X=X, mask=None, k=10, phi=0.5, phi_auto=False, normalize=False, n_gamma=20, fixed=(1e-3, 1e1),
-                    desc="plain n=200 p=10 4 Gaussian clusters, kNN k=10 w=exp(-0.5 d2), 20 gamma 1e-3..1e1")
+                    precision=1, desc="plain n=200 p=10 4 Gaussian clusters, kNN k=10 w=exp(-0.5 d2), "
+                                      "20 gamma 1e-3..1e1, FP64 path")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -452,7 +453,8 @@ def main():
     n, p = W["X"].shape
     Xd = torch.from_numpy(W["X"]).cuda()
     Md = torch.from_numpy(W["mask"]).cuda() if W["mask"] is not None else None
-    pr = ccx.Problem(Xd, Md, ccx.CCX_FP32)
+    prec = W.get("precision", ccx.CCX_FP32)
+    pr = ccx.Problem(Xd, Md, prec)
     pr.build_knn(W["k"], phi=W.get("phi", 0.0), phi_auto=W.get("phi_auto", False), normalize=W["normalize"])
     ei, ej, w = pr.get_edges()
     m = int(ei.size)
@@ -610,7 +612,8 @@ def main():
     # (24 B), the projection sweep reads R and A and writes A (12 B), the edge
     # pass reads A, A' and U (12 B); per edge, s and the CSR entry (12 B) and
     # the new ||b|| (4 B)
-    alg_bytes = 48.0 * n * p + 16.0 * m
+    es = 8.0 if prec == ccx.CCX_FP64 else 4.0             # matrix element bytes (the model is per FP32 element)
+    alg_bytes = 48.0 * (es / 4.0) * n * p + 16.0 * m
     # this kernel's own minimum traffic: per matrix entry, A (hi, lo) read and
     # written, Delta_{m-1} read, Delta_m written, X read, one mask bit, and
     # (missing entries) two offsets read and written; per edge, the momentum
@@ -627,7 +630,7 @@ def main():
         Lh = np.empty((G, n), np.int32)
 
         def e2e_step():
-            q = ccx.Problem(W["X"], W["mask"], ccx.CCX_FP32)
+            q = ccx.Problem(W["X"], W["mask"], prec)
             q.build_knn(W["k"], phi=W.get("phi", 0.0), phi_auto=W.get("phi_auto", False), normalize=W["normalize"])
             _, _, st2, _ = q.solve_path(gammas, opts, U_out=Uh, labels_out=Lh)
             q.close()
@@ -661,7 +664,7 @@ def main():
         hbm = peaks.get("hbm_gbs")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if prec == ccx.CCX_FP64 else "f32", "data": "synthetic",
                 "config": run_config(W, m, ws),
                 "iters_per_step": int(statistics.median(iters)),
                 "per_gamma_iters_converged_fused": per_gamma,
@@ -670,7 +673,8 @@ def main():
                              "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_note,
                              "kernel": "pd_slice_kernel", "slice_ms": slice_ms, "reduce_ms": reduce_ms,
                              "alg_bytes_per_launch": alg_bytes,
-                             "alg_bytes_model": "48 n p + 16 |E| (one projection sweep per iteration)",
+                             "alg_bytes_model": "48 n p + 16 |E| (one projection sweep per iteration; doubled "
+                                                "per element on the FP64 path)",
                              "own_min_bytes_per_launch": own_bytes,
                              "frac_own_bytes": own_bytes / (slice_ms * 1e-3) / 1e9 / hbm,
                              "target_frac": 0.6,

@@ -97,6 +97,24 @@ def test_genotype_multislice_against_stored_oracle(ccx, genotype, variant):
     pr.close()
 
 
+def test_genotype_multislice_fp64_path(ccx, genotype):
+    """The FP64 instantiation of the iteration kernel on the same multi-slice case (double rows, float
+    per-edge partials, so near-threshold decisions go through the double recompute): U within 1e-6 of
+    the oracle (the stored values are float32, 6e-8 relative), fused flags and labels as above."""
+    z = genotype
+    n, p = z["X"].shape
+    pr = ccx.Problem(z["X"], z["mask"], ccx.CCX_FP64)
+    pr.set_edges(z["ei"], z["ej"], z["w"])
+    U, L, F, stats = run(ccx, pr, z["gammas"], z["ei"].size)
+    for g in range(len(z["gammas"])):
+        ref = z["U"][g].astype(np.float64)
+        err = np.linalg.norm(U[g] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-6, (g, err)
+        assert stats[g]["converged"] in (1, 2), (g, stats[g])
+        check_fused(F[g], L[g], z, g, n, "genotype fp64")
+    pr.close()
+
+
 def test_genotype_staging_variants_identical_and_grid_cap(ccx, genotype):
     """The two staging variants compute the same arithmetic in the same order: bit-identical results.
     A grid of 16 CTAs (39 or 40 slices each) still matches the oracle."""
