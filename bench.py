@@ -427,6 +427,8 @@ def main():
     ap.add_argument("--slice-variant", type=int, default=0, choices=[0, 1, 2],
                     help="staging of the iteration kernel's slices: 0 automatic, 1 double buffer where it fits, "
                          "2 single buffer")
+    ap.add_argument("--anderson", type=int, default=0, metavar="M",
+                    help="Anderson mixing of the MM map over M map outputs before any fusion (0: off)")
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -450,6 +452,7 @@ def main():
     W = workload(args.workload)
     opts = ccx.opts_default()
     opts.slice_variant = args.slice_variant
+    opts.anderson = args.anderson
     n, p = W["X"].shape
     Xd = torch.from_numpy(W["X"]).cuda()
     Md = torch.from_numpy(W["mask"]).cuda() if W["mask"] is not None else None
@@ -591,7 +594,8 @@ def main():
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
             iters.append(sum(s["iters"] for s in stats))
-            per_gamma = [(int(s["iters"]), int(s["converged"]), int(s["n_fused"])) for s in stats]
+            per_gamma = [(int(s["iters"]), int(s["converged"]), int(s["n_fused"]), int(s["mixing_iters"]))
+                         for s in stats]
     launches = ccx.kernel_launches() - l0
     if dist:
         dist.barrier()
@@ -667,7 +671,8 @@ def main():
                 "vs_baseline": None, "dtype": "f64" if prec == ccx.CCX_FP64 else "f32", "data": "synthetic",
                 "config": run_config(W, m, ws),
                 "iters_per_step": int(statistics.median(iters)),
-                "per_gamma_iters_converged_fused": per_gamma,
+                "per_gamma_iters_converged_fused_mixed": per_gamma,
+                "anderson": args.anderson,
                 "solves_per_s": ws / t_max,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_note,

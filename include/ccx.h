@@ -123,6 +123,13 @@ typedef struct {
                           double from the rows of the projection before the decision, so a fuse
                           decision does not rest on the rounding of float partial sums.  Default
                           1e-5; 0 disables the recompute. */
+    int anderson;      /* 0 (default): off.  1..8: while the path has not started fusing (no edge fused at
+                          the end of the previous gamma), each gamma starts with Anderson mixing of the
+                          MM map over the last `anderson` map outputs (the momentum is off meanwhile);
+                          the restart rule takes over when an edge fuses, when the mixed residual stops
+                          falling, or after 3000 iterations, and its stopping test decides convergence
+                          as usual.  The fixed point is the same; the mixing keeps 2 x anderson + 1
+                          float copies of the matrix on the device.  The ccx_shard_* calls ignore it. */
 } ccx_opts;
 
 /* Per-gamma statistics. */
@@ -141,6 +148,7 @@ typedef struct {
     int n_recomputed;  /* edges whose fuse decision at the returned iterate was taken from the double
                           recompute of ||b_ij|| (see ccx_opts.fuse_delta) */
     long long recomputes;  /* double recomputes of ||b_ij|| over all iterations of this gamma */
+    int mixing_iters;  /* iterations of this gamma spent in the Anderson mixing phase (ccx_opts.anderson) */
 } ccx_gamma_stats;
 
 /* Fill *o with the defaults listed above. */

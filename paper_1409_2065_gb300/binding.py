@@ -37,14 +37,14 @@ class Opts(C.Structure):
     _fields_ = [("rho_scale", C.c_double), ("eps_rel", C.c_double), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("accelerate", C.c_int), ("chunk", C.c_int), ("extrapolate", C.c_int),
                 ("stream_edges", C.c_int), ("slice_variant", C.c_int), ("max_ctas", C.c_int),
-                ("fuse_delta", C.c_double)]
+                ("fuse_delta", C.c_double), ("anderson", C.c_int)]
 
 
 class GammaStats(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("n_fused", C.c_int), ("n_clusters", C.c_int),
                 ("gamma", C.c_double), ("rho", C.c_double), ("eps", C.c_double), ("d_final", C.c_double),
                 ("err_est", C.c_double), ("seconds", C.c_double), ("n_recomputed", C.c_int),
-                ("recomputes", C.c_longlong)]
+                ("recomputes", C.c_longlong), ("mixing_iters", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -166,6 +166,18 @@ struct ccx_problem {
     int max_ctas = 0;
     int tuned_G = 0;             // grid chosen by ccx_tune_grid (0: none), used when the options set no cap
     double delta_fuse = 1e-5;
+    // Anderson mixing (opts.anderson): history length of the current call, the one the
+    // buffers were sized for, the one the captured graph was built with, and the buffers
+    int aa_use = 0, aa_alloc = 0, graph_aa = -1;
+    float* aaR = nullptr;
+    float* aaG = nullptr;
+    float* aaS = nullptr;
+    float* aaRt = nullptr;
+    float* aaGt = nullptr;
+    float* aaSt = nullptr;
+    float* aaPt = nullptr;
+    double* aaP = nullptr;
+    int last_fused = -1;         // fused edges at the end of the last solved gamma (-1: none yet)
 };
 
 namespace {
@@ -187,6 +199,18 @@ void free_path(ccx_problem* pr) {
     cudaFree(pr->Aprev2_lo);
     pr->Aprev = pr->Aprev2 = nullptr;
     pr->Aprev_lo = pr->Aprev2_lo = nullptr;
+    cudaFree(pr->aaR);
+    cudaFree(pr->aaG);
+    cudaFree(pr->aaS);
+    cudaFree(pr->aaRt);
+    cudaFree(pr->aaGt);
+    cudaFree(pr->aaSt);
+    cudaFree(pr->aaPt);
+    cudaFree(pr->aaP);
+    pr->aaR = pr->aaG = pr->aaS = pr->aaRt = pr->aaGt = pr->aaSt = pr->aaPt = nullptr;
+    pr->aaP = nullptr;
+    pr->aa_alloc = 0;
+    pr->last_fused = -1;
     cudaFree(pr->Pnb);
     cudaFree(pr->Ps);
     cudaFree(pr->nb);
@@ -572,6 +596,16 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.n_ext = 0;
     P.ext_len = 0;
     P.p = (int)pr->p;
+    const bool aa = pr->aa_use > 0 && pr->aa_alloc == pr->aa_use;
+    P.aaR = aa ? pr->aaR : nullptr;
+    P.aaG = aa ? pr->aaG : nullptr;
+    P.aaS = aa ? pr->aaS : nullptr;
+    P.aaRt = aa ? pr->aaRt : nullptr;
+    P.aaGt = aa ? pr->aaGt : nullptr;
+    P.aaSt = aa ? pr->aaSt : nullptr;
+    P.aaPt = aa ? pr->aaPt : nullptr;
+    P.aaP = aa ? pr->aaP : nullptr;
+    P.aa_blocks = aa ? 4 * pr->num_sms : 0;
     P.ei = pr->d_ei;
     P.ej = pr->d_ej;
     P.w = pr->d_w;
@@ -624,6 +658,7 @@ void apply_opts(ccx_problem* pr, const ccx_opts& o) {
     pr->variant = o.slice_variant;
     pr->max_ctas = o.max_ctas > 0 ? o.max_ctas : pr->tuned_G;
     pr->delta_fuse = o.fuse_delta;
+    pr->aa_use = o.anderson;
 }
 
 ccx_status ensure_path(ccx_problem* pr) {
@@ -688,9 +723,47 @@ ccx_status ensure_path(ccx_problem* pr) {
     return CCX_OK;
 }
 
+// Buffers of the Anderson mixing for history aa_use (sized once per length; a
+// change drops the captured graph, which holds their addresses).
+ccx_status ensure_aa(ccx_problem* pr) {
+    const int m = pr->aa_use;
+    if (m <= 0 || pr->aa_alloc == m) return CCX_OK;
+    if (pr->graph) {
+        CUDA_TRY(cudaStreamSynchronize(pr->work));
+        cudaGraphExecDestroy(pr->graph);
+        pr->graph = nullptr;
+        pr->graph_chunk = 0;
+    }
+    CUDA_TRY(cudaStreamSynchronize(pr->work));
+    cudaFree(pr->aaR);
+    cudaFree(pr->aaG);
+    cudaFree(pr->aaS);
+    cudaFree(pr->aaRt);
+    cudaFree(pr->aaGt);
+    cudaFree(pr->aaSt);
+    cudaFree(pr->aaPt);
+    cudaFree(pr->aaP);
+    pr->aaR = pr->aaG = pr->aaS = pr->aaRt = pr->aaGt = pr->aaSt = pr->aaPt = nullptr;
+    pr->aaP = nullptr;
+    pr->aa_alloc = 0;
+    const size_t nl = (size_t)pr->n * pr->ld;
+    const size_t LE = (size_t)pr->le * kSliceThreads;
+    CUDA_TRY(dalloc(&pr->aaR, (size_t)m * nl));
+    CUDA_TRY(dalloc(&pr->aaG, (size_t)m * nl));
+    CUDA_TRY(dalloc(&pr->aaS, nl));
+    CUDA_TRY(dalloc(&pr->aaRt, (size_t)m * LE));
+    CUDA_TRY(dalloc(&pr->aaGt, (size_t)m * LE));
+    CUDA_TRY(dalloc(&pr->aaSt, LE));
+    CUDA_TRY(dalloc(&pr->aaPt, LE));
+    CUDA_TRY(dalloc(&pr->aaP, (size_t)4 * pr->num_sms * kAaDots));
+    pr->aa_alloc = m;
+    return CCX_OK;
+}
+
 bool graph_stale(const ccx_problem* pr, int chunk) {
     return !pr->graph || pr->graph_chunk != chunk || pr->graph_stream != pr->stream_edges ||
-           pr->graph_variant != pr->variant || pr->graph_G != pr->G || pr->graph_delta != pr->delta_fuse;
+           pr->graph_variant != pr->variant || pr->graph_G != pr->G || pr->graph_delta != pr->delta_fuse ||
+           pr->graph_aa != pr->aa_use;
 }
 
 ccx_status build_graph(ccx_problem* pr, int chunk) {
@@ -704,13 +777,17 @@ ccx_status build_graph(ccx_problem* pr, int chunk) {
     CUDA_TRY(cudaStreamBeginCapture(pr->work, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
     for (int k = 0; k < chunk && err == cudaSuccess; ++k) {
-        if (pr->precision == CCX_FP64)
+        if (pr->precision == CCX_FP64) {
             err = launch_pd_iteration_variant<double>(make_params<double>(pr), pr->variant, pr->work);
-        else
+            if (err == cudaSuccess) err = launch_pd_aa<double>(make_params<double>(pr), pr->work);
+        } else {
             err = launch_pd_iteration_variant<float>(make_params<float>(pr), pr->variant, pr->work);
+            if (err == cudaSuccess) err = launch_pd_aa<float>(make_params<float>(pr), pr->work);
+        }
     }
     cudaError_t e2 = cudaStreamEndCapture(pr->work, &g);
-    g_launches.fetch_sub(2ULL * (unsigned long long)chunk, std::memory_order_relaxed);  // captured, not launched
+    const unsigned long long kpi = pr->aa_use > 0 ? 4ULL : 2ULL;     // kernels per iteration
+    g_launches.fetch_sub(kpi * (unsigned long long)chunk, std::memory_order_relaxed);  // captured, not launched
     if (err != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return fail(CCX_ECUDA, "capturing the iteration graph failed: %s",
@@ -724,6 +801,7 @@ ccx_status build_graph(ccx_problem* pr, int chunk) {
     pr->graph_variant = pr->variant;
     pr->graph_G = pr->G;
     pr->graph_delta = pr->delta_fuse;
+    pr->graph_aa = pr->aa_use;
     return CCX_OK;
 }
 
@@ -804,8 +882,11 @@ ccx_status path_begin_gamma(PathRun& r) {
                                           quad ? reinterpret_cast<R*>(pr->Aprev2) : nullptr,
                                           quad ? pr->Aprev2_lo : nullptr, w0, w1, w2, pr->work));
     }
+    // the mixing phase only while the path has not started fusing: at a fusion
+    // transition the map is not smooth and the restart rule does better
+    const int aa_m = (r.o.anderson > 0 && pr->last_fused <= 0) ? r.o.anderson : 0;
     CUDA_TRY(launch_pd_begin_gamma<R>(make_params<R>(pr), gamma, r.rho, r.eps, r.o.tol, r.o.max_iter,
-                                      r.o.accelerate, scale_floor, pr->work));
+                                      r.o.accelerate, scale_floor, aa_m, pr->work));
     r.launched = r.checked = 0;
     r.phase = PathRun::kIterate;
     return CCX_OK;
@@ -820,6 +901,8 @@ ccx_status path_open(PathRun& r) {
     s = enter(pr);
     if (s != CCX_OK) return s;
     s = ensure_path(pr);
+    if (s != CCX_OK) return s;
+    s = ensure_aa(pr);
     if (s != CCX_OK) return s;
     IterParams<R> P = make_params<R>(pr);
     if (!pr->path_started) {
@@ -856,7 +939,7 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
     if (r.phase == PathRun::kIterate) {
         while (r.launched - r.checked < 2) {
             CUDA_TRY(cudaGraphLaunch(pr->graph, pr->work));
-            count_launches(2ULL * (unsigned long long)pr->graph_chunk);
+            count_launches((pr->graph_aa > 0 ? 4ULL : 2ULL) * (unsigned long long)pr->graph_chunk);
             CUDA_TRY(cudaMemcpyAsync(&pr->st_host[r.launched & 1], pr->st, sizeof(PdState), cudaMemcpyDeviceToHost,
                                      pr->work));
             CUDA_TRY(cudaEventRecord(pr->ev_chunk[r.launched & 1], pr->work));
@@ -878,6 +961,7 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
         // The chunk queued behind the finished one returns at once; everything
         // below is ordered after it on the work stream.
         if (r.final.converged == 0) r.all_conv = false;
+        pr->last_fused = r.final.n_fused;
         r.conv_hist[2] = r.conv_hist[1];
         r.conv_hist[1] = r.conv_hist[0];
         r.conv_hist[0] = r.final.converged;
@@ -942,6 +1026,7 @@ ccx_status path_step(PathRun& r, bool block, bool* progressed) {
             S.err_est = r.final.err_est;
             S.n_recomputed = r.final.n_recomputed;
             S.recomputes = r.final.recompute_total;
+            S.mixing_iters = r.final.aa_total;
             S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t0).count();
         }
         ++r.g;
@@ -1004,6 +1089,7 @@ ccx_status resolve_opts(const ccx_problem* pr, const ccx_opts* opts, ccx_opts* o
     if (o->slice_variant < 0 || o->slice_variant > 2) return fail(CCX_EINVAL, "slice_variant must be 0, 1 or 2");
     if (o->max_ctas < 0) return fail(CCX_EINVAL, "max_ctas must be >= 0");
     if (!(o->fuse_delta >= 0.0 && o->fuse_delta < 1.0)) return fail(CCX_EINVAL, "fuse_delta must be in [0, 1)");
+    if (o->anderson < 0 || o->anderson > kAaMax) return fail(CCX_EINVAL, "anderson must be in [0, %d]", kAaMax);
     return CCX_OK;
 }
 
@@ -1033,6 +1119,7 @@ void ccx_opts_default(ccx_opts* o) {
     o->slice_variant = 0;
     o->max_ctas = 0;
     o->fuse_delta = 1e-5;
+    o->anderson = 0;
 }
 
 const char* ccx_last_error(void) { return g_err.c_str(); }
@@ -1875,6 +1962,7 @@ ccx_status ccx_shard_begin_gamma(ccx_problem* pr, double gamma, const ccx_opts* 
     ShardState& sh = *pr->shard;
     ccx_status s = resolve_opts(pr, opts, &sh.run.o);
     if (s != CCX_OK) return s;
+    sh.run.o.anderson = 0;   // the shard calls run the plain iteration kernels only
     apply_opts(pr, sh.run.o);
     s = check_limits(pr);
     if (s != CCX_OK) return s;
@@ -1990,7 +2078,7 @@ ccx_status time_iterations_impl(ccx_problem* pr, double gamma, int n_iter, const
             pr->path_started = true;
         }
         // tol < 0: neither stopping rule fires; max_iter leaves room for all iterations
-        CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, -1.0, n_iter + 1, o.accelerate, 0.0, pr->work));
+        CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, -1.0, n_iter + 1, o.accelerate, 0.0, 0, pr->work));
         for (int k = 0; k < n_iter; ++k) {
             CUDA_TRY(cudaEventRecord(ev[3 * k], pr->work));
             CUDA_TRY(launch_pd_slice_variant<R>(P, pr->variant, pr->work));
@@ -2083,6 +2171,7 @@ ccx_status ccx_reset_path(ccx_problem* pr) {
     g_err.clear();
     if (!pr) return fail(CCX_EINVAL, "problem is NULL");
     pr->path_started = false;
+    pr->last_fused = -1;
     if (pr->shard) pr->shard->open = false;
     return CCX_OK;
 }

@@ -33,6 +33,9 @@ constexpr int kNoiseWindows = 8;       // consecutive such windows before stoppi
 constexpr int kStallWindows = 16;      // windows without a 2x residual decrease over kRateWindows before a plateau exit
 constexpr double kStallTolFactor = 100.0;  // a plateau exit needs the rate-based error estimate within this x tol
 constexpr double kFuseMargin = 1e-5;   // relative margin of a "clearly fused" edge (mu w d >= rho ||b|| (1 + margin))
+constexpr int kAaMax = 8;              // longest history of the Anderson mixing
+constexpr int kAaBudget = 3000;        // mixing iterations of one gamma before the hand-over
+constexpr int kAaDots = 2 * kAaMax + 3;  // partial sums per block of pd_aa_update_kernel
 
 // Scalar partial slots written by each CTA of the iteration kernel.
 enum : int {
@@ -77,6 +80,23 @@ struct PdState {
     unsigned int counter; // arrival counter of the reduce kernel's blocks
     int n_recomputed;     // edges of the last iteration whose fuse decision came from the FP64 recompute
     long long recompute_total;  // FP64 recomputes over the current gamma's iterations
+    // Anderson mixing of the MM map (aa_kernels.cu): the state z = (A, t, alpha) of
+    // an iteration is replaced by a combination of the last aa_m map outputs, from
+    // the start of a gamma until the hand-over to the restart rule
+    int aa_m;             // history length (0: no mixing in this problem)
+    int aa_on;            // mixing active in the current gamma
+    int aa_len;           // history entries held (<= aa_m)
+    int aa_head;          // ring slot the next entry takes
+    int aa_iters;         // iterations of the current mixing phase
+    int aa_have_prev;     // the previous iteration's residual is held
+    unsigned int aa_counter;  // arrival counter of pd_aa_update_kernel's blocks
+    int aa_total;         // mixing iterations of the current gamma (reported)
+    double aa_M[kAaMax][kAaMax];  // Gram matrix of the residual differences, by ring slot
+    double aa_g[kAaMax];          // mixing coefficients of the next mix, by ring slot (0 off the history)
+    double aa_win[4];             // residual norm at the ends of the last four windows
+    double aa_ra_prev;            // alpha part of the previous residual
+    double aa_sa;                 // alpha part of the last step z_k - z_(k-1)
+    double aa_RA[kAaMax], aa_GA[kAaMax];  // alpha parts of the ring entries
 };
 
 template <typename R>
@@ -128,6 +148,19 @@ struct IterParams {
     const double* ext_part;
     int n_ext;
     long long ext_len;
+    // Anderson mixing buffers (float): aa_m rings of residual differences and of
+    // map-output differences for A (n*ld each) and t (le*T each, edge-sweep order),
+    // the last step z_k - z_(k-1) (A and t parts), the previous residual's t part,
+    // and the per-block partial sums of pd_aa_update_kernel
+    float* aaR;
+    float* aaG;
+    float* aaS;
+    float* aaRt;
+    float* aaGt;
+    float* aaSt;
+    float* aaPt;
+    double* aaP;
+    int aa_blocks;
     int n, p, ld, ldw, m, nslices, G;
     int la, le, nslots;         // run lengths of the two sweeps; node-sweep partial slots
     int stream_edges;           // 1: per-entry arrays of the sweeps stay in global memory
@@ -137,9 +170,10 @@ struct IterParams {
 // (defined in pd_kernels.cu; all asynchronous on `s`)
 template <typename R>
 cudaError_t launch_pd_init(const IterParams<R>& P, const R* Y0, cudaStream_t s);
+// aa_m > 0 starts the gamma with an Anderson mixing phase of history aa_m
 template <typename R>
 cudaError_t launch_pd_begin_gamma(const IterParams<R>& P, double gamma, double rho, double eps, double tol,
-                                  int max_iter, int accelerate, double scale_floor, cudaStream_t s);
+                                  int max_iter, int accelerate, double scale_floor, int aa_m, cudaStream_t s);
 template <typename R>
 cudaError_t launch_pd_iteration(const IterParams<R>& P, cudaStream_t s);
 template <typename R>
@@ -159,6 +193,10 @@ template <typename R>
 cudaError_t launch_pd_slice_variant(const IterParams<R>& P, int variant, cudaStream_t s);
 template <typename R>
 cudaError_t launch_pd_iteration_variant(const IterParams<R>& P, int variant, cudaStream_t s);
+// Anderson mixing (aa_kernels.cu), launched after the reduction of every iteration;
+// both kernels return at once unless the current gamma is in its mixing phase
+template <typename R>
+cudaError_t launch_pd_aa(const IterParams<R>& P, cudaStream_t s);
 // per-position and scalar partials of this problem's CTAs, summed over CTAs in a
 // fixed order into out (le*T + kNumScalarPartials doubles): one shard's share
 template <typename R>

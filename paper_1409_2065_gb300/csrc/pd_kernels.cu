@@ -734,7 +734,11 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     st->d_last = d;
     st->alpha2 = st->alpha1;
     st->alpha1 = d / (d + rho);
-    if (st->accelerate) {
+    if (st->aa_on) {
+        // Anderson mixing phase (aa_kernels.cu): the plain map, no momentum
+        st->k_mom = 0;
+        st->beta = 0.0;
+    } else if (st->accelerate) {
         // adaptive restart (O'Donoghue-Candes gradient test) on the projection:
         // drop the momentum when <a_start - A_m, A_m - A_{m-1}> > 0
         if (rs > 0.0) st->k_mom = 0;
@@ -755,7 +759,7 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     if (step > st->blk_max) st->blk_max = step;
     if (noise > st->noise_max) st->noise_max = noise;
     if (dres > st->dmax) st->dmax = dres;
-    if (st->iter % kConvWindow == 0) {
+    if (st->iter % kConvWindow == 0 && !st->aa_on) {
         // Error estimate.  The correction ||A_m - A_start|| is the map's residual
         // at the extrapolated point: ~ eta * error for the slowest mode (gap eta),
         // and unlike the step it does not jump when the momentum restarts.  The
@@ -903,11 +907,13 @@ __global__ void pd_init_kernel(IterParams<R> P, const R* Y0, size_t total) {
         st->d_last = 0.0;
         st->n_recomputed = 0;
         st->recompute_total = 0;
+        st->aa_on = 0;
+        st->aa_total = 0;
     }
 }
 
 __global__ void pd_begin_gamma_kernel(PdState* st, double gamma, double rho, double eps, double tol, int max_iter,
-                                      int accelerate, double scale_floor) {
+                                      int accelerate, double scale_floor, int aa_m) {
     st->scale_floor = scale_floor;
     st->gamma = gamma;
     st->rho = rho;
@@ -934,6 +940,18 @@ __global__ void pd_begin_gamma_kernel(PdState* st, double gamma, double rho, dou
     st->counter = 0u;
     st->n_recomputed = 0;
     st->recompute_total = 0;
+    st->aa_m = aa_m;
+    st->aa_on = aa_m > 0 ? 1 : 0;
+    st->aa_len = 0;
+    st->aa_head = 0;
+    st->aa_iters = 0;
+    st->aa_total = 0;
+    st->aa_have_prev = 0;
+    st->aa_counter = 0u;
+    st->aa_ra_prev = 0.0;
+    st->aa_sa = 0.0;
+    for (int q = 0; q < 4; ++q) st->aa_win[q] = 0.0;
+    for (int j = 0; j < kAaMax; ++j) st->aa_g[j] = 0.0;
 }
 
 template <typename R>
@@ -1064,9 +1082,9 @@ cudaError_t launch_pd_init(const IterParams<R>& P, const R* Y0, cudaStream_t s) 
 
 template <typename R>
 cudaError_t launch_pd_begin_gamma(const IterParams<R>& P, double gamma, double rho, double eps, double tol,
-                                  int max_iter, int accelerate, double scale_floor, cudaStream_t s) {
+                                  int max_iter, int accelerate, double scale_floor, int aa_m, cudaStream_t s) {
     count_launches(1);
-    pd_begin_gamma_kernel<<<1, 1, 0, s>>>(P.st, gamma, rho, eps, tol, max_iter, accelerate, scale_floor);
+    pd_begin_gamma_kernel<<<1, 1, 0, s>>>(P.st, gamma, rho, eps, tol, max_iter, accelerate, scale_floor, aa_m);
     return cudaGetLastError();
 }
 
@@ -1152,9 +1170,9 @@ template cudaError_t launch_pd_iteration<double>(const IterParams<double>&, cuda
 template cudaError_t launch_pd_init<float>(const IterParams<float>&, const float*, cudaStream_t);
 template cudaError_t launch_pd_init<double>(const IterParams<double>&, const double*, cudaStream_t);
 template cudaError_t launch_pd_begin_gamma<float>(const IterParams<float>&, double, double, double, double, int, int,
-                                                  double, cudaStream_t);
+                                                  double, int, cudaStream_t);
 template cudaError_t launch_pd_begin_gamma<double>(const IterParams<double>&, double, double, double, double, int, int,
-                                                   double, cudaStream_t);
+                                                   double, int, cudaStream_t);
 template cudaError_t launch_pd_extrapolate<float>(const IterParams<float>&, float*, float*, float*, float*, double,
                                                   double, double, cudaStream_t);
 template cudaError_t launch_pd_extrapolate<double>(const IterParams<double>&, double*, float*, double*, float*, double,

@@ -414,3 +414,27 @@ def test_standardize_matches_oracle(ccx, precision):
     assert pr.get_edges()[0].size == 0
     assert np.max(np.abs(pr.get_start() - Y)) <= 1e-6
     pr.close()
+
+
+def test_size_limits_and_empty_grid(ccx):
+    """The documented limits answer with CCX_EUNSUPPORTED (7) and a message, without running a kernel
+    on sizes the kernels do not handle: n > 65535 for the iteration kernel (16-bit node indices), n > 4096
+    for the kNN build.  An empty gamma grid returns at once with nothing written."""
+    n = 70000
+    X = np.linspace(0.0, 1.0, n, dtype=np.float32).reshape(n, 1)
+    pr = ccx.Problem(X)
+    ei = np.arange(n - 1)
+    pr.set_edges(ei, ei + 1, np.ones(n - 1))
+    with pytest.raises(ccx.CcxError) as e:
+        pr.solve_path([0.1])
+    assert e.value.status == 7 and "65535" in e.value.message
+    with pytest.raises(ccx.CcxError) as e:
+        pr.build_knn(3, phi=1.0)
+    assert e.value.status == 7 and "4096" in e.value.message
+    pr.close()
+    Xs, _ = synth.gaussian_mixture(20, 3, 2, seed=3)
+    pr = ccx.Problem(Xs)
+    pr.build_knn(3, phi=0.1)
+    U, labels, stats, st = pr.solve_path([])
+    assert st == 0 and U.shape == (0, 20, 3) and labels.shape == (0, 20)
+    pr.close()

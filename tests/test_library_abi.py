@@ -33,7 +33,8 @@ def test_defaults_and_version():
     import paper_1409_2065_gb300 as ccx
     o = ccx.opts_default()
     assert (o.rho_scale, o.eps_rel, o.tol, o.max_iter, o.accelerate, o.chunk, o.extrapolate, o.stream_edges,
-            o.slice_variant, o.max_ctas, o.fuse_delta) == (2.0, 1e-3, 1e-6, 200000, 1, 64, 1, 0, 0, 0, 1e-5)
+            o.slice_variant, o.max_ctas, o.fuse_delta, o.anderson) == (2.0, 1e-3, 1e-6, 200000, 1, 64, 1, 0, 0, 0,
+                                                                       1e-5, 0)
     assert "sm_103a" in ccx.version()
 
 
