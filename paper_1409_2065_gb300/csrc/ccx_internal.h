@@ -236,6 +236,10 @@ struct KnnResult {
 cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi, int phi_auto, int normalize,
                       cudaStream_t s, KnnResult* out, std::string* err, const double* geo = nullptr,
                       double alpha = 1.0, int geodesic = 0, int gram = 0);
+// union of the kNN lists (nbr, nd2: device, n x kk, from knn_build's list pass), phi and the
+// weights on the device (knn_weights.cu); the edges come back to the host sorted by (ei, ej)
+cudaError_t knn_union_weights(const int* nbr, const double* nd2, int n, int kk, double phi, int phi_auto,
+                              int normalize, cudaStream_t s, KnnResult* out);
 // principal axes of Y_0 (pc_kernels.cu): axes q x p doubles (device), variances on the host
 int pc_max_axes();
 cudaError_t pc_axes(const float* Y0f, const double* mean, int n, int p, int ld, int q, double* axes, double* var_h,

@@ -12,7 +12,7 @@
 //    exactly from the rows (double differences and sums in a fixed order),
 //    and the k smallest by (d2, j) are kept: ties go to the smaller index.
 // 4. The union i ~_k j, phi, the weights and the normalisation are formed on
-//    the host from the exact d2 (knn_build).
+//    the device from the exact d2 (knn_weights.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -436,71 +436,9 @@ cudaError_t knn_build(const float* Y0f, int n, int p, int ld, int k, double phi,
         cudaFree(nbr);
         cudaFree(nd2);
     };
-    std::vector<int> hn((size_t)n * kk);
-    std::vector<double> hd((size_t)n * kk);
-    if ((e = cudaMemcpyAsync(hn.data(), nbr, sizeof(int) * hn.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cleanup(), e;
-    if ((e = cudaMemcpyAsync(hd.data(), nd2, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, s)) !=
-        cudaSuccess)
-        return cleanup(), e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cleanup(), e;
+    e = knn_union_weights(nbr, nd2, n, kk, phi, phi_auto, normalize, s, out);
     cleanup();
-    // union i ~_k j, sorted by (i, j)
-    std::vector<std::pair<long long, double>> pairs;
-    pairs.reserve(hn.size());
-    for (int i = 0; i < n; ++i)
-        for (int r = 0; r < kk; ++r) {
-            const int j = hn[(size_t)i * kk + r];
-            const int a = std::min(i, j), b = std::max(i, j);
-            pairs.push_back({(long long)a * n + b, hd[(size_t)i * kk + r]});
-        }
-    std::sort(pairs.begin(), pairs.end(),
-              [](const std::pair<long long, double>& x, const std::pair<long long, double>& y) {
-                  return x.first < y.first;
-              });
-    for (size_t q = 0; q < pairs.size(); ++q) {
-        if (q > 0 && pairs[q].first == pairs[q - 1].first) continue;
-        out->ei.push_back((int)(pairs[q].first / n));
-        out->ej.push_back((int)(pairs[q].first % n));
-        out->d2.push_back(pairs[q].second);
-    }
-    const size_t m = out->d2.size();
-    if (phi_auto) {
-        std::vector<double> t = out->d2;
-        std::sort(t.begin(), t.end());
-        double med = 0.0;
-        if (m > 0) med = (m % 2) ? t[m / 2] : 0.5 * (t[m / 2 - 1] + t[m / 2]);
-        phi = med > 0 ? 1.0 / med : 0.0;
-    }
-    out->phi = phi;
-    out->w.resize(m);
-    if (normalize && m > 0) {
-        const double dmin = *std::min_element(out->d2.begin(), out->d2.end());
-        double tot = 0.0;
-        for (size_t q = 0; q < m; ++q) {
-            out->w[q] = std::exp(-phi * (out->d2[q] - dmin));
-            tot += out->w[q];
-        }
-        for (size_t q = 0; q < m; ++q) out->w[q] /= tot;
-    } else {
-        for (size_t q = 0; q < m; ++q) out->w[q] = std::exp(-phi * out->d2[q]);
-    }
-    // drop exact zeros
-    size_t keep = 0;
-    for (size_t q = 0; q < m; ++q) {
-        if (out->w[q] > 0.0) {
-            out->ei[keep] = out->ei[q];
-            out->ej[keep] = out->ej[q];
-            out->d2[keep] = out->d2[q];
-            out->w[keep] = out->w[q];
-            ++keep;
-        }
-    }
-    out->ei.resize(keep);
-    out->ej.resize(keep);
-    out->d2.resize(keep);
-    out->w.resize(keep);
-    return cudaSuccess;
+    return e;
 }
 
 }  // namespace ccx

@@ -276,6 +276,45 @@ def test_knn_all_pairs(ccx):
     assert np.array_equal(ei, oei) and np.allclose(w, ow, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("rule", ["auto_norm", "auto", "fixed_norm", "fixed", "underflow_norm"])
+@pytest.mark.parametrize("n,k", [(61, 4), (100, 6)])
+def test_knn_weight_rules_on_device(ccx, rule, n, k):
+    """The union, phi (automatic: 1 / median d2, odd and even edge counts), the Gaussian weights and
+    their normalisation, all formed on the device: edges equal the oracle's exactly, weights within
+    1e-12, and a rebuild is bit-identical.  With phi = 2000 / median (normalised) most weights
+    underflow to zero and those edges are dropped, as in the oracle."""
+    X, mask, _ = synth.genotype_like(n, 40, 3, seed=n + k, fst=0.05, frac_missing=0.05)
+    X64 = X.astype(np.float64)
+    _, _, _, d2, phi_med = O.knn_gaussian_weights(X64, mask, k, "auto", False)
+    auto = rule.startswith("auto")
+    norm = rule.endswith("norm")
+    phi = "auto" if auto else (2000.0 * phi_med if rule.startswith("underflow") else 0.7 * phi_med)
+    oei, oej, ow, _, _ = O.knn_gaussian_weights(X64, mask, k, phi, norm)
+    if rule.startswith("underflow"):
+        assert 0 < oei.size < d2.size            # some weights are exactly zero
+    got = []
+    for _ in range(2):
+        pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+        pr.build_knn(k, phi=0.0 if auto else phi, phi_auto=auto, normalize=norm)
+        got.append(pr.get_edges())
+        pr.close()
+    ei, ej, w = got[0]
+    assert np.array_equal(ei, oei) and np.array_equal(ej, oej)
+    assert np.allclose(w, ow, rtol=1e-12, atol=0)
+    assert np.array_equal(w, got[1][2])
+    if norm:
+        assert abs(w.sum() - 1.0) < 1e-12
+
+
+def test_knn_edge_counts_of_both_parities():
+    """The automatic phi above takes the median of an odd and of an even number of edges."""
+    counts = set()
+    for n, k in [(61, 4), (100, 6)]:
+        X, mask, _ = synth.genotype_like(n, 40, 3, seed=n + k, fst=0.05, frac_missing=0.05)
+        counts.add(O.knn_gaussian_weights(X.astype(np.float64), mask, k, "auto", False)[0].size % 2)
+    assert counts == {0, 1}
+
+
 def test_edge_cases(ccx):
     # a single case: no edges, U = X
     X1 = np.array([[1.0, -2.0, 3.0]], np.float32)
