@@ -427,8 +427,13 @@ def main():
     ap.add_argument("--slice-variant", type=int, default=0, choices=[0, 1, 2],
                     help="staging of the iteration kernel's slices: 0 automatic, 1 double buffer where it fits, "
                          "2 single buffer")
-    ap.add_argument("--anderson", type=int, default=0, metavar="M",
-                    help="Anderson mixing of the MM map over M map outputs before any fusion (0: off)")
+    ap.add_argument("--anderson", type=int, default=5, metavar="M",
+                    help="Anderson mixing of the MM map over M map outputs while the previous gamma had no "
+                         "fused edge (0: off, the plain restart rule throughout; default 5)")
+    ap.add_argument("--mixing-only", type=int, default=0, metavar="K",
+                    help="build the workload, run K individually launched MM iterations with Anderson mixing "
+                         "(history --anderson) at the first gamma and print the mean times of the iteration, "
+                         "reduction and mixing kernels (K < 320 keeps every iteration mixed)")
     ap.add_argument("--iterations-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations at the middle gamma "
                          "and print the two kernels' mean times (a short target for a profiler)")
@@ -555,6 +560,14 @@ def main():
         print(json.dumps({"metric": "seconds to the smallest connected k", "workload": W["desc"], "k_max": args.min_k,
                           "k": k_gpu, "oracle_k": k_ref, "gpu_seconds": t_gpu, "oracle_seconds": t_ref,
                           "oracle_cores": os.cpu_count()}), flush=True)
+        return
+    if args.mixing_only:
+        if args.anderson < 1:
+            raise SystemExit("--mixing-only needs --anderson >= 1")
+        slice_ms, reduce_ms, mix_ms = pr.time_iterations_mixing(float(gammas[0]), args.mixing_only, opts)
+        print(json.dumps({"workload": W["desc"], "iterations": args.mixing_only, "anderson": args.anderson,
+                          "gamma_index": 0, "slice_ms": slice_ms, "reduce_ms": reduce_ms, "mix_ms": mix_ms}),
+              flush=True)
         return
     if args.iterations_only:
         slice_ms, reduce_ms = pr.time_iterations(float(gammas[len(gammas) // 2]), args.iterations_only, opts)

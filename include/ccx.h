@@ -471,6 +471,19 @@ ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const 
                                double* reduce_ms);
 
 /*
+ * Instrumentation: as ccx_time_iterations, with the Anderson mixing kernels
+ * (history opts->anderson, which must be >= 1) launched after every
+ * iteration; *mix_ms is their mean time per iteration.  Mixing stays on while
+ * no edge is fused and for at most 3000 iterations, stagnation aside (it is
+ * tested from the 320th iteration on): time it at a gamma below the first
+ * fusion with n_iter < 320, or the later iterations measure only the kernels'
+ * early exit.  Same errors as ccx_time_iterations; CCX_EINVAL also for a NULL
+ * opts or mix_ms.
+ */
+ccx_status ccx_time_iterations_mixing(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts,
+                                      double* slice_ms, double* reduce_ms, double* mix_ms);
+
+/*
  * Instrumentation (no counterpart in the paper; host only, needs no GPU): the
  * work layout the iteration kernel uses for a sorted edge set (0 <= ei < ej <
  * n, ordered by (ei, ej), no duplicates; n <= 65535).  The kernel's T threads

@@ -82,6 +82,8 @@ _sigs = {
     "ccx_problem_destroy": (C.c_int, [_P]),
     "ccx_time_iterations": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]),
+    "ccx_time_iterations_mixing": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ccx_kernel_launches": (C.c_uint64, []),
     "ccx_sweep_plan": (C.c_int, [C.c_int64, C.c_int64, _P, _P, C.c_int, _P, _P, _P, _P]),
     "ccx_last_error": (C.c_char_p, []),
@@ -503,6 +505,15 @@ def time_iterations(h, gamma: float, n_iter: int, opts: Opts | None = None):
     return a.value, b.value
 
 
+def time_iterations_mixing(h, gamma: float, n_iter: int, opts: Opts):
+    """(mean ms of the iteration kernel, of the reduction kernel, of the two Anderson mixing kernels)
+    over n_iter iterations with mixing history opts.anderson."""
+    a, b, c = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.ccx_time_iterations_mixing(h, float(gamma), int(n_iter), C.byref(opts), C.byref(a), C.byref(b),
+                                           C.byref(c)))
+    return a.value, b.value, c.value
+
+
 def sweep_plan(n: int, ei, ej, precision=CCX_FP32):
     """Work layout of the iteration kernel (host only): (T, la, le, nslots, node_row, node_nbr, edge_id),
     the arrays indexed by position k * T + t (-1 past the end of a run)."""
@@ -571,6 +582,9 @@ class Problem:
 
     def time_iterations(self, gamma, n_iter, opts=None):
         return time_iterations(self.h, gamma, n_iter, opts)
+
+    def time_iterations_mixing(self, gamma, n_iter, opts):
+        return time_iterations_mixing(self.h, gamma, n_iter, opts)
 
     def close(self):
         if self.h:

@@ -2054,20 +2054,27 @@ namespace {
 // n_iter MM iterations of the current warm-start state at penalty gamma with
 // the stopping test off, each kernel launched alone between CUDA events on the
 // work stream; mean milliseconds of the slice and reduce kernels.
+// mix_ms: NULL (the plain map), or the mean time of the two Anderson mixing kernels, which then run
+// after every iteration with history o.anderson (from the state the path holds, at this gamma)
 ccx_status time_iterations_impl(ccx_problem* pr, double gamma, int n_iter, const ccx_opts& o, double* slice_ms,
-                                double* reduce_ms) {
+                                double* reduce_ms, double* mix_ms = nullptr) {
     ccx_status s = check_limits(pr);
     if (s != CCX_OK) return s;
     s = enter(pr);
     if (s != CCX_OK) return s;
     s = ensure_path(pr);
     if (s != CCX_OK) return s;
+    const int aa_m = mix_ms ? o.anderson : 0;
+    if (aa_m > 0) {
+        s = ensure_aa(pr);
+        if (s != CCX_OK) return s;
+    }
     const bool fp64 = pr->precision == CCX_FP64;
     double rho = o.rho_scale * (pr->nyc + gamma * pr->nw);
     if (!(rho > 0.0)) rho = o.rho_scale;
     double eps = (o.eps_rel * pr->nyc) * (o.eps_rel * pr->nyc);
     if (!(eps > 0.0)) eps = o.eps_rel * o.eps_rel;
-    std::vector<cudaEvent_t> ev(3 * (size_t)n_iter);
+    std::vector<cudaEvent_t> ev(4 * (size_t)n_iter);
     for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
     auto body = [&](auto tag) -> ccx_status {
         using R = decltype(tag);
@@ -2078,25 +2085,31 @@ ccx_status time_iterations_impl(ccx_problem* pr, double gamma, int n_iter, const
             pr->path_started = true;
         }
         // tol < 0: neither stopping rule fires; max_iter leaves room for all iterations
-        CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, -1.0, n_iter + 1, o.accelerate, 0.0, 0, pr->work));
+        CUDA_TRY(launch_pd_begin_gamma<R>(P, gamma, rho, eps, -1.0, n_iter + 1, o.accelerate, 0.0, aa_m,
+                                          pr->work));
         for (int k = 0; k < n_iter; ++k) {
-            CUDA_TRY(cudaEventRecord(ev[3 * k], pr->work));
+            CUDA_TRY(cudaEventRecord(ev[4 * k], pr->work));
             CUDA_TRY(launch_pd_slice_variant<R>(P, pr->variant, pr->work));
-            CUDA_TRY(cudaEventRecord(ev[3 * k + 1], pr->work));
+            CUDA_TRY(cudaEventRecord(ev[4 * k + 1], pr->work));
             CUDA_TRY(launch_pd_reduce<R>(P, pr->work));
-            CUDA_TRY(cudaEventRecord(ev[3 * k + 2], pr->work));
+            CUDA_TRY(cudaEventRecord(ev[4 * k + 2], pr->work));
+            if (aa_m > 0) CUDA_TRY(launch_pd_aa<R>(P, pr->work));
+            CUDA_TRY(cudaEventRecord(ev[4 * k + 3], pr->work));
         }
         CUDA_TRY(cudaStreamSynchronize(pr->work));
-        double a = 0.0, b = 0.0;
+        double a = 0.0, b = 0.0, c = 0.0;
         for (int k = 0; k < n_iter; ++k) {
-            float t1 = 0.f, t2 = 0.f;
-            CUDA_TRY(cudaEventElapsedTime(&t1, ev[3 * k], ev[3 * k + 1]));
-            CUDA_TRY(cudaEventElapsedTime(&t2, ev[3 * k + 1], ev[3 * k + 2]));
+            float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&t1, ev[4 * k], ev[4 * k + 1]));
+            CUDA_TRY(cudaEventElapsedTime(&t2, ev[4 * k + 1], ev[4 * k + 2]));
+            CUDA_TRY(cudaEventElapsedTime(&t3, ev[4 * k + 2], ev[4 * k + 3]));
             a += t1;
             b += t2;
+            c += t3;
         }
         *slice_ms = a / n_iter;
         *reduce_ms = b / n_iter;
+        if (mix_ms) *mix_ms = c / n_iter;
         return CCX_OK;
     };
     s = fp64 ? body(double{}) : body(float{});
@@ -2119,6 +2132,20 @@ ccx_status ccx_time_iterations(ccx_problem* pr, double gamma, int n_iter, const 
     if (s != CCX_OK) return s;
     apply_opts(pr, o);
     return time_iterations_impl(pr, gamma, n_iter, o, slice_ms, reduce_ms);
+}
+
+ccx_status ccx_time_iterations_mixing(ccx_problem* pr, double gamma, int n_iter, const ccx_opts* opts,
+                                      double* slice_ms, double* reduce_ms, double* mix_ms) {
+    g_err.clear();
+    if (!pr || !opts || !slice_ms || !reduce_ms || !mix_ms) return fail(CCX_EINVAL, "NULL argument");
+    if (!std::isfinite(gamma) || gamma < 0.0) return fail(CCX_EINVAL, "gamma must be finite and >= 0");
+    if (n_iter < 1) return fail(CCX_EINVAL, "n_iter must be >= 1");
+    ccx_opts o;
+    ccx_status s = resolve_opts(pr, opts, &o);
+    if (s != CCX_OK) return s;
+    if (o.anderson < 1) return fail(CCX_EINVAL, "opts->anderson must be >= 1 to time the mixing kernels");
+    apply_opts(pr, o);
+    return time_iterations_impl(pr, gamma, n_iter, o, slice_ms, reduce_ms, mix_ms);
 }
 
 ccx_status ccx_tune_grid(ccx_problem* pr, int g_min, int* g_out, double* ms_out) {

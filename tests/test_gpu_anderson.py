@@ -62,6 +62,28 @@ def test_genotype_multislice_with_mixing(ccx, m):
     pr.close()
 
 
+def test_allpairs_multislice_with_mixing(ccx):
+    """The stored all-pairs case (n = 32, p = 5000, 496 edges, eight or nine slices per CTA) with
+    mixing: stored rows element by element, every row's norm, fused flags and labels."""
+    z = dict(np.load(os.path.join(GOLDEN, "allpairs_n32_p5000.npz")))
+    X, _ = synth.expression_like(32, 5000, 3, 150, seed=62)
+    n = X.shape[0]
+    pr = ccx.Problem(X, None, ccx.CCX_FP32)
+    pr.set_edges(z["ei"], z["ej"], z["w"])
+    U, L, F, stats = _solve(ccx, pr, z["gammas"], _opts(ccx, 5))
+    rows = z["rows"]
+    for g in range(len(z["gammas"])):
+        ref = z["U_rows"][g].astype(np.float64)
+        err = np.linalg.norm(U[g][rows] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-4, (g, err, stats[g])
+        rn = np.linalg.norm(U[g].astype(np.float64), axis=1)
+        assert np.max(np.abs(rn - z["row_norm"][g])) <= 1e-4 * z["fro"][g] / np.sqrt(n), g
+        assert stats[g]["converged"] in (1, 2), (g, stats[g])
+        check_fused(F[g], L[g], z, g, n, "allpairs aa5")
+    assert stats[0]["mixing_iters"] > 0
+    pr.close()
+
+
 @pytest.mark.parametrize("precision,utol", [(1, 1e-6), (0, 1e-4)])
 def test_plain_workload_with_mixing(ccx, precision, utol):
     """n = 200, p = 10, 20 gammas against the stored oracle values; the 17 gammas before the first
@@ -126,3 +148,17 @@ def test_batch_with_mixing_equals_alone(ccx):
         assert np.array_equal(Us[i], alone[i][0]) and np.array_equal(Ls[i], alone[i][1]), i
     for pr in probs:
         pr.close()
+
+
+def test_time_iterations_mixing(ccx):
+    """The instrumentation call times the mixing kernels (positive mean times at a gamma before any
+    fusion) and refuses a history of 0."""
+    X, mask, _ = synth.genotype_like(120, 64, 3, seed=5, fst=0.05, frac_missing=0.05)
+    pr = ccx.Problem(X, mask, ccx.CCX_FP32)
+    pr.build_knn(6, phi_auto=True, normalize=True)
+    g0 = pr.fusion_scale()
+    a, b, c = pr.time_iterations_mixing(0.01 * g0, 20, _opts(ccx, 4))
+    assert a > 0 and b > 0 and c > 0
+    with pytest.raises(ccx.CcxError):
+        pr.time_iterations_mixing(0.01 * g0, 20, _opts(ccx, 0))
+    pr.close()
