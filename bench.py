@@ -44,7 +44,8 @@ UNIT = "edge-updates/s"
 def workload(name: str):
     if name == "genotype":
         X, mask, _ = synth.genotype_like(1000, 10000, 5, seed=1, fst=0.05, frac_missing=0.05)
-        return dict(X=X, mask=mask, k=10, phi_auto=True, normalize=True, n_gamma=50, lo=3e-2, hi=3.0,
+        # Anderson mixing: the path has 17 gammas before the first fusion, where it cuts iterations
+        return dict(X=X, mask=mask, k=10, phi_auto=True, normalize=True, n_gamma=50, lo=3e-2, hi=3.0, anderson=5,
                     desc="genotype-like n=1000 p=10000, 5 pops Balding-Nichols Fst=0.05, 5% missing, "
                          "kNN k=10 phi=1/median d2 normalised, 50 gamma in [0.03,3]*gamma0")
     if name == "expression":
@@ -427,9 +428,10 @@ def main():
     ap.add_argument("--slice-variant", type=int, default=0, choices=[0, 1, 2],
                     help="staging of the iteration kernel's slices: 0 automatic, 1 double buffer where it fits, "
                          "2 single buffer")
-    ap.add_argument("--anderson", type=int, default=5, metavar="M",
+    ap.add_argument("--anderson", type=int, default=None, metavar="M",
                     help="Anderson mixing of the MM map over M map outputs while the previous gamma had no "
-                         "fused edge (0: off, the plain restart rule throughout; default 5)")
+                         "fused edge (0: off, the plain restart rule throughout); default: the workload's "
+                         "setting (5 for genotype, whose path has many gammas before fusion; 0 for the others)")
     ap.add_argument("--mixing-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations with Anderson mixing "
                          "(history --anderson) at the first gamma and print the mean times of the iteration, "
@@ -455,6 +457,8 @@ def main():
         run_serve(args, ccx, torch, rank)
         return
     W = workload(args.workload)
+    if args.anderson is None:
+        args.anderson = W.get("anderson", 0)
     opts = ccx.opts_default()
     opts.slice_variant = args.slice_variant
     opts.anderson = args.anderson
@@ -643,11 +647,15 @@ def main():
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        Uh = np.empty((G, n, p), np.float32)
-        Lh = np.empty((G, n), np.int32)
+        # host buffers in pinned (page-locked) memory, allocated once outside the timed region as a
+        # serving process would: the inputs are copied in and U and the labels copied out every step
+        Xh = torch.from_numpy(W["X"]).pin_memory().numpy()
+        Mh = torch.from_numpy(W["mask"]).pin_memory().numpy() if W["mask"] is not None else None
+        Uh = torch.empty((G, n, p), dtype=torch.float32, pin_memory=True).numpy()
+        Lh = torch.empty((G, n), dtype=torch.int32, pin_memory=True).numpy()
 
         def e2e_step():
-            q = ccx.Problem(W["X"], W["mask"], prec)
+            q = ccx.Problem(Xh, Mh, prec)
             q.build_knn(W["k"], phi=W.get("phi", 0.0), phi_auto=W.get("phi_auto", False), normalize=W["normalize"])
             _, _, st2, _ = q.solve_path(gammas, opts, U_out=Uh, labels_out=Lh)
             q.close()
@@ -666,10 +674,10 @@ def main():
             upds.append(dist_sum(m * p * sum(s["iters"] for s in st2), dist))
         k = int(np.argsort(tes)[len(tes) // 2])
         te, upd = tes[k], upds[k]
-        h2d = W["X"].nbytes + (W["mask"].nbytes if W["mask"] is not None else 0)
+        h2d = Xh.nbytes + (Mh.nbytes if Mh is not None else 0)
         d2h = Uh.nbytes + Lh.nbytes
         e2e = {"value": upd / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "seconds_per_step": te, "solves_per_s": ws / te, "runs": runs}
+               "seconds_per_step": te, "solves_per_s": ws / te, "runs": runs, "host_memory": "pinned"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
