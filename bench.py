@@ -432,6 +432,9 @@ def main():
                     help="Anderson mixing of the MM map over M map outputs while the previous gamma had no "
                          "fused edge (0: off, the plain restart rule throughout); default: the workload's "
                          "setting (5 for genotype, whose path has many gammas before fusion; 0 for the others)")
+    ap.add_argument("--fuse-delta", type=float, default=None, metavar="D",
+                    help="relative band around the fusion threshold in which an edge's norm is recomputed "
+                         "in double before its fuse decision (library default 1e-5; 0 turns it off)")
     ap.add_argument("--mixing-only", type=int, default=0, metavar="K",
                     help="build the workload, run K individually launched MM iterations with Anderson mixing "
                          "(history --anderson) at the first gamma and print the mean times of the iteration, "
@@ -462,6 +465,8 @@ def main():
     opts = ccx.opts_default()
     opts.slice_variant = args.slice_variant
     opts.anderson = args.anderson
+    if args.fuse_delta is not None:
+        opts.fuse_delta = args.fuse_delta
     n, p = W["X"].shape
     Xd = torch.from_numpy(W["X"]).cuda()
     Md = torch.from_numpy(W["mask"]).cuda() if W["mask"] is not None else None
@@ -613,6 +618,7 @@ def main():
             iters.append(sum(s["iters"] for s in stats))
             per_gamma = [(int(s["iters"]), int(s["converged"]), int(s["n_fused"]), int(s["mixing_iters"]))
                          for s in stats]
+            recomputes = int(sum(s["recomputes"] for s in stats))
     launches = ccx.kernel_launches() - l0
     if dist:
         dist.barrier()
@@ -694,6 +700,7 @@ def main():
                 "iters_per_step": int(statistics.median(iters)),
                 "per_gamma_iters_converged_fused_mixed": per_gamma,
                 "anderson": args.anderson,
+                "fp64_recomputes_per_step": recomputes,
                 "solves_per_s": ws / t_max,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_note,

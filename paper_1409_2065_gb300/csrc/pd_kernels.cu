@@ -545,10 +545,79 @@ __device__ __forceinline__ double dm_sum(const double* ps, int G, long long stri
 
 // Per edge-sweep position: the 8-group strided sum of the per-CTA ||b||^2
 // partials (group q takes CTAs q, q + 8, ...), then the groups in order.
+// The loads are issued four at a time ahead of their (in-order) additions, so a
+// thread waits for one L2 round trip per four partials instead of per partial.
 __device__ __forceinline__ double nb2_group_sum(const float* Pnb, int G, int LE, int pos, int grp) {
     double s = 0.0;
-    for (int g = grp; g < G; g += kRedGroups) s += (double)Pnb[(size_t)g * LE + pos];
+    int g = grp;
+    for (; g + 3 * kRedGroups < G; g += 4 * kRedGroups) {
+        const float v0 = Pnb[(size_t)g * LE + pos];
+        const float v1 = Pnb[(size_t)(g + kRedGroups) * LE + pos];
+        const float v2 = Pnb[(size_t)(g + 2 * kRedGroups) * LE + pos];
+        const float v3 = Pnb[(size_t)(g + 3 * kRedGroups) * LE + pos];
+        s += (double)v0;
+        s += (double)v1;
+        s += (double)v2;
+        s += (double)v3;
+    }
+    for (; g < G; g += kRedGroups) s += (double)Pnb[(size_t)g * LE + pos];
     return s;
+}
+
+template <typename R>
+__device__ void last_block_update(PdState* st, const double (*redv)[7], const unsigned long long* hsh,
+                                  int nthreads, double d, double rho);
+
+// This thread's share of ||a_i - a_j||^2 in double over the p columns of two rows
+// of A (hi + lo on the FP32 path), rows starting at offsets oi and oj (multiples
+// of 32 elements): groups of four columns, two groups in flight per step so that
+// a thread waits for one L2 round trip per eight columns; the last p mod 4
+// columns go to the first threads.  The order of the additions is fixed.
+template <typename R>
+__device__ __forceinline__ double row_diff_sq(const R* __restrict__ hi, const float* __restrict__ lo, size_t oi,
+                                              size_t oj, int p, int tid) {
+    constexpr bool FF = std::is_same<R, float>::value;
+    using V4 = Vec<R, 4>;
+    using F4 = Vec<float, 4>;
+    constexpr int T = kReduceThreads;
+    const int ng = p / 4;
+    double acc0 = 0.0, acc1 = 0.0;
+    auto group = [&](int g, double& acc) {
+        const V4 hi4 = *reinterpret_cast<const V4*>(hi + oi + 4 * (size_t)g);
+        const V4 hj4 = *reinterpret_cast<const V4*>(hi + oj + 4 * (size_t)g);
+        F4 li4, lj4;
+        if constexpr (FF) {
+            li4 = *reinterpret_cast<const F4*>(lo + oi + 4 * (size_t)g);
+            lj4 = *reinterpret_cast<const F4*>(lo + oj + 4 * (size_t)g);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double ai = (double)hi4.v[c], aj = (double)hj4.v[c];
+            if constexpr (FF) {
+                ai += (double)li4.v[c];
+                aj += (double)lj4.v[c];
+            }
+            const double dd = ai - aj;
+            acc = fma(dd, dd, acc);
+        }
+    };
+    int g = tid;
+    for (; g + T < ng; g += 2 * T) {
+        group(g, acc0);
+        group(g + T, acc1);
+    }
+    if (g < ng) group(g, acc0);
+    const int c = 4 * ng + tid;
+    if (c < p) {
+        double ai = (double)hi[oi + c], aj = (double)hi[oj + c];
+        if constexpr (FF) {
+            ai += (double)lo[oi + c];
+            aj += (double)lo[oj + c];
+        }
+        const double dd = ai - aj;
+        acc0 = fma(dd, dd, acc0);
+    }
+    return acc0 + acc1;
 }
 
 template <typename R>
@@ -574,6 +643,16 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     const int lane = tid % kRedEdges, grp = tid / kRedEdges;
     const int pos = blockIdx.x * kRedEdges + lane;
     const int e = pos < LE ? P.eid[pos] : -1;
+    // this edge's weight, previous t and node-sweep positions, requested before the
+    // partial sums so that their round trip to L2 overlaps with those loads
+    R told = (R)0;
+    int2 qp = make_int2(0, 0);
+    double we = 0.0;
+    if (grp == 0 && e >= 0) {
+        we = P.w[e];
+        told = P.t[st->par][2 * (size_t)LA + 2 * (size_t)pos];
+        qp = P.posA[pos];
+    }
     double s = 0.0;
     if (e >= 0) {
         if (ext) {
@@ -588,21 +667,13 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     const double gamma = st->gamma, rho = st->rho;
     double lhs = 0.0;
     bool near = false;
-    // this edge's previous t and its node-sweep positions, requested with its weight
-    // so that one round trip to L2 serves them all
-    R told = (R)0;
-    int2 qp = make_int2(0, 0);
-    if (grp == 0 && e >= 0) {
-        told = P.t[st->par][2 * (size_t)LA + 2 * (size_t)pos];
-        qp = P.posA[pos];
-    }
     if (grp == 0) {
         double nb = 0.0;
         if (e >= 0) {
             double tot = 0.0;
             for (int g = 0; g < kRedGroups; ++g) tot += part[g][lane];
             nb = sqrt(tot);
-            lhs = gamma * P.w[e] * d;
+            lhs = gamma * we * d;
             const double rhs = rho * nb;
             // the prox's zero test mu w d >= rho ||b|| within the rounding of the
             // float partial sums: decide it from ||b|| recomputed in double
@@ -626,17 +697,7 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
             nm &= nm - 1;
             const int ee = P.eid[blockIdx.x * kRedEdges + l];
             const size_t oi = (size_t)P.ei[ee] * P.ld, oj = (size_t)P.ej[ee] * P.ld;
-            double acc = 0.0;
-            for (int c = tid; c < P.p; c += kReduceThreads) {
-                double ai = (double)hi[oi + c], aj = (double)hi[oj + c];
-                if constexpr (FF) {
-                    ai += (double)lo[oi + c];
-                    aj += (double)lo[oj + c];
-                }
-                const double dd = ai - aj;
-                acc = fma(dd, dd, acc);
-            }
-            const double tot = block_sum(acc, red);
+            const double tot = block_sum(row_diff_sq<R>(hi, lo, oi, oj, P.p, tid), red);
             if (tid == 0) s_nb[l] = sqrt(tot);
             __syncthreads();
         }
@@ -713,8 +774,26 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
 #pragma unroll
         for (int k = 0; k < kNv; ++k) redv[tid >> 5][k] = v[k];
     hsh[tid] = hash_l;
+    // the scalar state, copied to shared memory for thread 0's serial update: one
+    // coalesced read and write instead of a dependent global round trip per field
+    static_assert(sizeof(PdState) % 8 == 0, "PdState is copied as 8-byte words");
+    constexpr int kStWords = (int)(sizeof(PdState) / 8);
+    __shared__ unsigned long long s_state[kStWords];
+    for (int k = tid; k < kStWords; k += blockDim.x)
+        s_state[k] = reinterpret_cast<const unsigned long long*>(P.st)[k];
     __syncthreads();
-    if (tid != 0) return;
+    if (tid == 0) last_block_update<R>(reinterpret_cast<PdState*>(s_state), redv, hsh, blockDim.x, d, rho);
+    __syncthreads();
+    for (int k = tid; k < kStWords; k += blockDim.x) reinterpret_cast<unsigned long long*>(P.st)[k] = s_state[k];
+}
+
+// Thread 0 of the reduction's last block: the iteration's scalar state update
+// (d_m, alpha, momentum, the fused-set stability and the stopping rule) on the
+// state `st` held in shared memory.
+template <typename R>
+__device__ void last_block_update(PdState* st, const double (*redv)[7], const unsigned long long* hsh,
+                                  int nthreads, double d, double rho) {
+    constexpr int kNv = 7;
     double tv[kNv];
 #pragma unroll
     for (int k = 0; k < kNv; ++k) {
@@ -725,7 +804,7 @@ __global__ void __launch_bounds__(kReduceThreads) pd_reduce_kernel(IterParams<R>
     const unsigned long long nf = (unsigned long long)tv[5];
     const unsigned long long nrec = (unsigned long long)tv[6];
     unsigned long long hash = 0ULL;
-    for (int k = 0; k < (int)blockDim.x; ++k) hash += hsh[k];
+    for (int k = 0; k < nthreads; ++k) hash += hsh[k];
     const double unit = sizeof(R) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     const double noise = unit * sqrt(nzs);
     st->iter += 1;
