@@ -123,7 +123,7 @@ typedef struct {
                           double from the rows of the projection before the decision, so a fuse
                           decision does not rest on the rounding of float partial sums.  Default
                           1e-5; 0 disables the recompute. */
-    int anderson;      /* 0 (default): off.  1..8: while the path has not started fusing (no edge fused at
+    int anderson;      /* 0 (default): off.  1..16: while the path has not started fusing (no edge fused at
                           the end of the previous gamma), each gamma starts with Anderson mixing of the
                           MM map over the last `anderson` map outputs (the momentum is off meanwhile);
                           the restart rule takes over when an edge fuses, when the mixed residual stops

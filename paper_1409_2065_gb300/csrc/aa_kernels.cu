@@ -42,11 +42,19 @@ template <typename T>
 struct alignas(sizeof(T) * 4) Quad {
     T v[4];
 };
-constexpr int kSlotRR = 0;                 // <dR_new, dR_j>, j = 0 .. kAaMax - 1
-constexpr int kSlotRr = kAaMax;            // <dR_j, r_k>
-constexpr int kSlotNN = 2 * kAaMax;        // <dR_new, dR_new>
-constexpr int kSlotNr = 2 * kAaMax + 1;    // <dR_new, r_k>
-constexpr int kSlotrr = 2 * kAaMax + 2;    // <r_k, r_k>
+// Partial inner products of the update, for kernels whose rings hold at most M
+// entries (M = 8 or kAaMax: the history length picks the instantiation, so a
+// short history does not carry the registers of a long one).
+template <int M>
+struct AaSlots {
+    static_assert(M <= kAaMax, "ring bound above the state's history arrays");
+    static constexpr int RR = 0;            // <dR_new, dR_j>, j = 0 .. M - 1
+    static constexpr int Rr = M;            // <dR_j, r_k>
+    static constexpr int NN = 2 * M;        // <dR_new, dR_new>
+    static constexpr int Nr = 2 * M + 1;    // <dR_new, r_k>
+    static constexpr int rr = 2 * M + 2;    // <r_k, r_k>
+    static constexpr int D = 2 * M + 3;     // number of partial sums (<= kAaDots)
+};
 
 __device__ __forceinline__ double aa_warp_sum(double v) {
 #pragma unroll
@@ -87,27 +95,29 @@ __device__ __forceinline__ bool aa_old_valid(int j, int m, int len, int head) {
 // The last block's thread 0: the alpha parts of the differences, the Gram
 // matrix of the residual differences, the mixing coefficients (normal
 // equations with a small ridge, Cholesky in double) and the hand-over test.
+template <int M>
 __device__ void aa_finish(PdState* st, const double* tot, const bool* old, int m, int len, int head, bool have) {
+    using S = AaSlots<M>;
     const double ra = st->alpha1 - st->alpha2;   // alpha part of r_k (the reduction set alpha1 = G_k, alpha2 = z_k)
-    const double rr = tot[kSlotrr] + ra * ra;
+    const double rr = tot[S::rr] + ra * ra;
     int nlen = len, nhead = head;
-    double g[kAaMax];
-    for (int j = 0; j < kAaMax; ++j) g[j] = 0.0;
+    double g[M];
+    for (int j = 0; j < M; ++j) g[j] = 0.0;
     if (have) {
         const double dn = ra - st->aa_ra_prev;
-        double rR[kAaMax], Rr[kAaMax];
-        for (int j = 0; j < kAaMax; ++j) {
-            rR[j] = tot[kSlotRR + j];
-            Rr[j] = tot[kSlotRr + j];
+        double rR[M], Rr[M];
+        for (int j = 0; j < M; ++j) {
+            rR[j] = tot[S::RR + j];
+            Rr[j] = tot[S::Rr + j];
             if (old[j]) {
                 rR[j] += dn * st->aa_RA[j];
                 Rr[j] += st->aa_RA[j] * ra;
             }
         }
-        const double nn = tot[kSlotNN] + dn * dn, nr = tot[kSlotNr] + dn * ra;
+        const double nn = tot[S::NN] + dn * dn, nr = tot[S::Nr] + dn * ra;
         st->aa_RA[head] = dn;
         st->aa_GA[head] = st->aa_sa + dn;
-        for (int j = 0; j < kAaMax; ++j)
+        for (int j = 0; j < M; ++j)
             if (old[j]) {
                 st->aa_M[head][j] = rR[j];
                 st->aa_M[j][head] = rR[j];
@@ -115,9 +125,9 @@ __device__ void aa_finish(PdState* st, const double* tot, const bool* old, int m
         st->aa_M[head][head] = nn;
         // slots held after the update, oldest first
         nlen = len + 1 < m ? len + 1 : m;
-        int idx[kAaMax];
+        int idx[M];
         for (int a = 0; a < nlen; ++a) idx[a] = (head - (nlen - 1 - a) + m) % m;
-        double A[kAaMax][kAaMax], b[kAaMax], y[kAaMax];
+        double A[M][M], b[M], y[M];
         double tr = 0.0;
         for (int a = 0; a < nlen; ++a) {
             b[a] = idx[a] == head ? nr : Rr[idx[a]];
@@ -164,7 +174,7 @@ __device__ void aa_finish(PdState* st, const double* tot, const bool* old, int m
             nhead = 0;
         }
     }
-    for (int j = 0; j < kAaMax; ++j) st->aa_g[j] = g[j];
+    for (int j = 0; j < M; ++j) st->aa_g[j] = g[j];
     st->aa_len = nlen;
     st->aa_head = nhead;
     st->aa_ra_prev = ra;
@@ -182,7 +192,7 @@ __device__ void aa_finish(PdState* st, const double* tot, const bool* old, int m
     }
     if (st->n_fused > 0 || st->aa_iters >= kAaBudget || stagnant) {
         st->aa_on = 0;
-        for (int j = 0; j < kAaMax; ++j) st->aa_g[j] = 0.0;
+        for (int j = 0; j < M; ++j) st->aa_g[j] = 0.0;
         // the restart rule takes over from the map's last output with a fresh
         // momentum and a fresh rate estimate for its stopping test
         st->k_mom = 0;
@@ -200,8 +210,9 @@ __device__ void aa_finish(PdState* st, const double* tot, const bool* old, int m
     st->aa_counter = 0u;
 }
 
-template <typename R>
+template <typename R, int M>
 __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> P) {
+    using S = AaSlots<M>;
     PdState* st = P.st;
     if (st->done || !st->aa_on) return;
     const int m = st->aa_m, len = st->aa_len, head = st->aa_head, par = st->par;
@@ -215,13 +226,13 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> 
     // a thread's own products in float-float (the normal equations of the mixing
     // are ill-conditioned: successive residual differences are nearly parallel),
     // the blocks' sums in double
-    float fhi[kAaDots], flo[kAaDots];
+    float fhi[S::D], flo[S::D];
 #pragma unroll
-    for (int q = 0; q < kAaDots; ++q) fhi[q] = flo[q] = 0.f;
-    double acc[kAaDots];
-    bool old[kAaMax];
+    for (int q = 0; q < S::D; ++q) fhi[q] = flo[q] = 0.f;
+    double acc[S::D];
+    bool old[M];
 #pragma unroll
-    for (int j = 0; j < kAaMax; ++j) old[j] = have && aa_old_valid(j, m, len, head);
+    for (int j = 0; j < M; ++j) old[j] = have && aa_old_valid(j, m, len, head);
 
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t NL4 = NL / 4;
@@ -234,14 +245,14 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> 
         const Quad<R> r4 = rk4[k];
         if (!have) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) ff_dot((float)r4.v[c], (float)r4.v[c], fhi[kSlotrr], flo[kSlotrr]);
+            for (int c = 0; c < 4; ++c) ff_dot((float)r4.v[c], (float)r4.v[c], fhi[S::rr], flo[S::rr]);
             continue;
         }
         const Quad<R> p4 = rp4[k];
         const Quad<float> s4 = S4[k];
-        Quad<float> old4[kAaMax];
+        Quad<float> old4[M];
 #pragma unroll
-        for (int j = 0; j < kAaMax; ++j)
+        for (int j = 0; j < M; ++j)
             if (old[j]) old4[j] = R4[(size_t)j * NL4 + k];
         Quad<float> nr4, ng4;
 #pragma unroll
@@ -249,15 +260,15 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> 
             const float r = (float)r4.v[c];
             const float dn = (float)((double)r4.v[c] - (double)p4.v[c]);
 #pragma unroll
-            for (int j = 0; j < kAaMax; ++j) {
+            for (int j = 0; j < M; ++j) {
                 if (!old[j]) continue;
                 const float Rj = old4[j].v[c];
-                ff_dot(dn, Rj, fhi[kSlotRR + j], flo[kSlotRR + j]);
-                ff_dot(Rj, r, fhi[kSlotRr + j], flo[kSlotRr + j]);
+                ff_dot(dn, Rj, fhi[S::RR + j], flo[S::RR + j]);
+                ff_dot(Rj, r, fhi[S::Rr + j], flo[S::Rr + j]);
             }
-            ff_dot(dn, dn, fhi[kSlotNN], flo[kSlotNN]);
-            ff_dot(dn, r, fhi[kSlotNr], flo[kSlotNr]);
-            ff_dot(r, r, fhi[kSlotrr], flo[kSlotrr]);
+            ff_dot(dn, dn, fhi[S::NN], flo[S::NN]);
+            ff_dot(dn, r, fhi[S::Nr], flo[S::Nr]);
+            ff_dot(r, r, fhi[S::rr], flo[S::rr]);
             nr4.v[c] = dn;
             ng4.v[c] = s4.v[c] + dn;
         }
@@ -265,22 +276,22 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> 
         G4[(size_t)head * NL4 + k] = ng4;
     }
 #pragma unroll
-    for (int q = 0; q < kAaDots; ++q) acc[q] = (double)fhi[q] + (double)flo[q];
+    for (int q = 0; q < S::D; ++q) acc[q] = (double)fhi[q] + (double)flo[q];
     for (size_t pos = blockIdx.x * (size_t)blockDim.x + threadIdx.x; pos < (size_t)LE; pos += stride) {
         if (P.eid[pos] < 0) continue;
         const double r = (double)tp[2 * pos] - (double)tp[2 * pos + 1];
-        acc[kSlotrr] += r * r;
+        acc[S::rr] += r * r;
         if (have) {
             const double dn = r - (double)P.aaPt[pos];
 #pragma unroll
-            for (int j = 0; j < kAaMax; ++j) {
+            for (int j = 0; j < M; ++j) {
                 if (!old[j]) continue;
                 const double Rj = (double)P.aaRt[(size_t)j * LE + pos];
-                acc[kSlotRR + j] += dn * Rj;
-                acc[kSlotRr + j] += Rj * r;
+                acc[S::RR + j] += dn * Rj;
+                acc[S::Rr + j] += Rj * r;
             }
-            acc[kSlotNN] += dn * dn;
-            acc[kSlotNr] += dn * r;
+            acc[S::NN] += dn * dn;
+            acc[S::Nr] += dn * r;
             P.aaRt[(size_t)head * LE + pos] = (float)dn;
             P.aaGt[(size_t)head * LE + pos] = (float)((double)P.aaSt[pos] + dn);
         }
@@ -288,20 +299,20 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> 
     }
 
     // block sums in a fixed order: a shuffle tree per warp, then the warps in order
-    __shared__ double red[kAaWarps][kAaDots];
-    __shared__ double tot[kAaDots];
+    __shared__ double red[kAaWarps][S::D];
+    __shared__ double tot[S::D];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < kAaDots; ++q) {
+    for (int q = 0; q < S::D; ++q) {
         const double v = aa_warp_sum(acc[q]);
         if (lane == 0) red[wid][q] = v;
     }
     __syncthreads();
-    if (threadIdx.x < kAaDots) {
+    if (threadIdx.x < S::D) {
         double v = 0.0;
         for (int w = 0; w < kAaWarps; ++w) v += red[w][threadIdx.x];
-        P.aaP[(size_t)blockIdx.x * kAaDots + threadIdx.x] = v;
+        P.aaP[(size_t)blockIdx.x * S::D + threadIdx.x] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -314,17 +325,17 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> 
     __threadfence();
     // the blocks' partials: thread t takes blocks t, t + 256, ..., then a fixed-order block sum
 #pragma unroll
-    for (int q = 0; q < kAaDots; ++q) acc[q] = 0.0;
+    for (int q = 0; q < S::D; ++q) acc[q] = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
 #pragma unroll
-        for (int q = 0; q < kAaDots; ++q) acc[q] += P.aaP[(size_t)b * kAaDots + q];
+        for (int q = 0; q < S::D; ++q) acc[q] += P.aaP[(size_t)b * S::D + q];
 #pragma unroll
-    for (int q = 0; q < kAaDots; ++q) {
+    for (int q = 0; q < S::D; ++q) {
         const double v = aa_warp_sum(acc[q]);
         if (lane == 0) red[wid][q] = v;
     }
     __syncthreads();
-    if (threadIdx.x < kAaDots) {
+    if (threadIdx.x < S::D) {
         double v = 0.0;
         for (int w = 0; w < kAaWarps; ++w) v += red[w][threadIdx.x];
         tot[threadIdx.x] = v;
@@ -332,10 +343,10 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_update_kernel(IterParams<R> 
     __syncthreads();
     if (threadIdx.x != 0) return;
     // (continued in aa_finish: the last block's thread 0 solves and decides)
-    aa_finish(st, tot, old, m, len, head, have);
+    aa_finish<M>(st, tot, old, m, len, head, have);
 }
 
-template <typename R>
+template <typename R, int M>
 __global__ void __launch_bounds__(kAaThreads) pd_aa_mix_kernel(IterParams<R> P) {
     PdState* st = P.st;
     if (st->done || !st->aa_on) return;
@@ -343,11 +354,11 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_mix_kernel(IterParams<R> P) 
     const int m = st->aa_m, par = st->par;
     const int LA = P.la * kSliceThreads, LE = P.le * kSliceThreads;
     const size_t NL = (size_t)P.n * P.ld;
-    double g[kAaMax];
-    float gf[kAaMax];
-    bool use[kAaMax];
+    double g[M];
+    float gf[M];
+    bool use[M];
 #pragma unroll
-    for (int j = 0; j < kAaMax; ++j) {
+    for (int j = 0; j < M; ++j) {
         g[j] = j < m ? st->aa_g[j] : 0.0;
         gf[j] = (float)g[j];
         use[j] = g[j] != 0.0;
@@ -359,7 +370,7 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_mix_kernel(IterParams<R> P) 
     Quad<float>* __restrict__ S4 = reinterpret_cast<Quad<float>*>(P.aaS);
     bool any = false;
 #pragma unroll
-    for (int j = 0; j < kAaMax; ++j) any = any || use[j];
+    for (int j = 0; j < M; ++j) any = any || use[j];
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const size_t NL4 = NL / 4;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < NL4; k += stride) {
@@ -368,12 +379,12 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_mix_kernel(IterParams<R> P) 
         const Quad<R> r4 = rk4[k];
         float c[4] = {0.f, 0.f, 0.f, 0.f};
         if (any) {
-            Quad<float> gq[kAaMax];
+            Quad<float> gq[M];
 #pragma unroll
-            for (int j = 0; j < kAaMax; ++j)
+            for (int j = 0; j < M; ++j)
                 if (use[j]) gq[j] = G4[(size_t)j * NL4 + k];
 #pragma unroll
-            for (int j = 0; j < kAaMax; ++j)
+            for (int j = 0; j < M; ++j)
                 if (use[j])
 #pragma unroll
                     for (int q = 0; q < 4; ++q) c[q] = fmaf(gf[j], gq[j].v[q], c[q]);
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_mix_kernel(IterParams<R> P) 
         if (P.eid[pos] < 0) continue;
         double c = 0.0;
 #pragma unroll
-        for (int j = 0; j < kAaMax; ++j)
+        for (int j = 0; j < M; ++j)
             if (use[j]) c += g[j] * (double)P.aaGt[(size_t)j * LE + pos];
         const size_t e2 = 2 * (size_t)LA + 2 * pos;
         double tm = (double)tp[e2] - c;
@@ -418,7 +429,7 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_mix_kernel(IterParams<R> P) 
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double c = 0.0;
-        for (int j = 0; j < kAaMax; ++j)
+        for (int j = 0; j < M; ++j)
             if (use[j]) c += g[j] * st->aa_GA[j];
         double a1 = st->alpha1 - c;
         a1 = a1 < 0.0 ? 0.0 : (a1 >= 1.0 ? st->alpha1 : a1);
@@ -432,11 +443,20 @@ __global__ void __launch_bounds__(kAaThreads) pd_aa_mix_kernel(IterParams<R> P) 
 template <typename R>
 cudaError_t launch_pd_aa(const IterParams<R>& P, cudaStream_t s) {
     if (!P.aaR || P.aa_blocks < 1) return cudaSuccess;   // no mixing buffers: mixing is off for this problem
+    if (P.aa_hist < 1 || P.aa_hist > kAaMax) return cudaErrorInvalidValue;
     count_launches(2);
-    pd_aa_update_kernel<R><<<P.aa_blocks, kAaThreads, 0, s>>>(P);
+    if (P.aa_hist <= 8) {
+        pd_aa_update_kernel<R, 8><<<P.aa_blocks, kAaThreads, 0, s>>>(P);
+    } else {
+        pd_aa_update_kernel<R, kAaMax><<<P.aa_blocks, kAaThreads, 0, s>>>(P);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    pd_aa_mix_kernel<R><<<P.aa_blocks, kAaThreads, 0, s>>>(P);
+    if (P.aa_hist <= 8) {
+        pd_aa_mix_kernel<R, 8><<<P.aa_blocks, kAaThreads, 0, s>>>(P);
+    } else {
+        pd_aa_mix_kernel<R, kAaMax><<<P.aa_blocks, kAaThreads, 0, s>>>(P);
+    }
     return cudaGetLastError();
 }
 

@@ -606,6 +606,7 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.aaPt = aa ? pr->aaPt : nullptr;
     P.aaP = aa ? pr->aaP : nullptr;
     P.aa_blocks = aa ? 4 * pr->num_sms : 0;
+    P.aa_hist = aa ? pr->aa_use : 0;
     P.ei = pr->d_ei;
     P.ej = pr->d_ej;
     P.w = pr->d_w;

@@ -33,7 +33,7 @@ constexpr int kNoiseWindows = 8;       // consecutive such windows before stoppi
 constexpr int kStallWindows = 16;      // windows without a 2x residual decrease over kRateWindows before a plateau exit
 constexpr double kStallTolFactor = 100.0;  // a plateau exit needs the rate-based error estimate within this x tol
 constexpr double kFuseMargin = 1e-5;   // relative margin of a "clearly fused" edge (mu w d >= rho ||b|| (1 + margin))
-constexpr int kAaMax = 8;              // longest history of the Anderson mixing
+constexpr int kAaMax = 16;             // longest history of the Anderson mixing
 constexpr int kAaBudget = 3000;        // mixing iterations of one gamma before the hand-over
 constexpr int kAaDots = 2 * kAaMax + 3;  // partial sums per block of pd_aa_update_kernel
 
@@ -161,6 +161,7 @@ struct IterParams {
     float* aaPt;
     double* aaP;
     int aa_blocks;
+    int aa_hist;                // history length of the mixing buffers (selects the kernels' ring bound)
     int n, p, ld, ldw, m, nslices, G;
     int la, le, nslots;         // run lengths of the two sweeps; node-sweep partial slots
     int stream_edges;           // 1: per-entry arrays of the sweeps stay in global memory

@@ -42,7 +42,7 @@ def _solve(ccx, pr, gammas, o):
     return U, L, fused, stats
 
 
-@pytest.mark.parametrize("m", [3, 5])
+@pytest.mark.parametrize("m", [3, 5, 8, 16])
 def test_genotype_multislice_with_mixing(ccx, m):
     """The stored genotype-like case (n = 48, p = 2502, 5 % missing): the first gamma (no fusion) is
     mixed, the second starts mixed and hands over when its edges fuse, later ones are not mixed."""
@@ -161,4 +161,8 @@ def test_time_iterations_mixing(ccx):
     assert a > 0 and b > 0 and c > 0
     with pytest.raises(ccx.CcxError):
         pr.time_iterations_mixing(0.01 * g0, 20, _opts(ccx, 0))
+    a, b, c16 = pr.time_iterations_mixing(0.01 * g0, 20, _opts(ccx, 16))   # the long-history kernels
+    assert c16 > 0
+    with pytest.raises(ccx.CcxError):                 # above the longest history
+        pr.solve_path([0.01 * g0], _opts(ccx, 17))
     pr.close()
