@@ -271,10 +271,12 @@ def run_batch(args, ccx, torch, rank):
 
     probs = make()
     grids = [synth.log_grid(0.03 * pr.fusion_scale(), 3.0 * pr.fusion_scale(), args.batch_gammas) for pr in probs]
+    opts = ccx.opts_default()
+    opts.anderson = args.anderson or 0          # the same options in every arm
     # (1) one call per problem, one after another
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    seq = [pr.solve_path(g, device=True) for pr, g in zip(probs, grids)]
+    seq = [pr.solve_path(g, opts, device=True) for pr, g in zip(probs, grids)]
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     iters = sum(s["iters"] for r in seq for s in r[2])
@@ -284,7 +286,7 @@ def run_batch(args, ccx, torch, rank):
         pr.reset_path()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    Us, Ls, stats, status, _ = ccx.solve_batch(probs, grids, device=True, max_active=args.batch_active)
+    Us, Ls, stats, status, _ = ccx.solve_batch(probs, grids, opts, device=True, max_active=args.batch_active)
     torch.cuda.synchronize()
     t_bat = time.perf_counter() - t0
     same = all(torch.equal(Us[i], seq[i][0]) and torch.equal(Ls[i], seq[i][1]) for i in range(len(probs)))
@@ -299,7 +301,7 @@ def run_batch(args, ccx, torch, rank):
     torch.cuda.synchronize()
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
-    Ut, Lt, stt, status_t, _ = ccx.solve_batch(probs, grids, device=True, max_active=args.batch_active)
+    Ut, Lt, stt, status_t, _ = ccx.solve_batch(probs, grids, opts, device=True, max_active=args.batch_active)
     torch.cuda.synchronize()
     t_tb = time.perf_counter() - t0
     rel = max(float(torch.linalg.vector_norm(Ut[i][g] - seq[i][0][g]) / torch.linalg.vector_norm(seq[i][0][g]))
@@ -314,6 +316,7 @@ def run_batch(args, ccx, torch, rank):
             "speedup": t_seq / t_bat, "speedup_tuned_incl_tuning": t_seq / (t_tb + t_tune),
             "seconds_plain": t_seq, "seconds_batched": t_bat, "seconds_tuned": t_tb, "seconds_tuning": t_tune,
             "tuned_grids": tuned, "max_active": args.batch_active, "mm_iterations_plain": int(iters),
+            "anderson": int(opts.anderson),
             "sum_np": int(sum(n * p for n, p in sz)), "identical_results": bool(same),
             "tuned_max_rel_diff_U": rel, "tuned_problems_with_identical_labels": lab_same,
             "all_converged": bool(conv_seq and conv_t and all(s == 0 for s in status + status_t)),

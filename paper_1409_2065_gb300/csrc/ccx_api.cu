@@ -605,7 +605,11 @@ IterParams<R> make_params(ccx_problem* pr) {
     P.aaSt = aa ? pr->aaSt : nullptr;
     P.aaPt = aa ? pr->aaPt : nullptr;
     P.aaP = aa ? pr->aaP : nullptr;
-    P.aa_blocks = aa ? 4 * pr->num_sms : 0;
+    // mixing kernels: four blocks per SM, or fewer when the matrix has fewer groups of
+    // four entries than that many blocks have threads (small problems in a batch)
+    const size_t aa_quads = (size_t)pr->n * pr->ld / 4;
+    const size_t aa_need = (aa_quads + 255) / 256;
+    P.aa_blocks = aa ? (int)std::max<size_t>(1, std::min<size_t>(aa_need, (size_t)4 * pr->num_sms)) : 0;
     P.aa_hist = aa ? pr->aa_use : 0;
     P.ei = pr->d_ei;
     P.ej = pr->d_ej;
